@@ -1,0 +1,235 @@
+/*
+ * sellcs.h -- C ABI of the GB300 SELL-C-sigma augmented SpMMV library.
+ *
+ * The operation (GHOST, arxiv 1507.08101, Sec. "Kernel fusion"):
+ *
+ *     y = alpha (A - gamma I) x + beta y
+ *
+ * for a sparse A in SELL-C-sigma storage (Sec. "Sparse matrix storage") and
+ * dense block vectors x, y (Sec. "Dense matrices", "Block vectors"), optionally
+ * chained with the dot products <y,y>, <x,y>, <x,x> of every vector of the
+ * block and with z = delta z + eta y, each augmentation enabled on its own,
+ * all in one pass over the matrix.
+ *
+ * General conventions
+ *  - Every function returns SP_OK (0) or a negative SP_ERR_* code; nothing
+ *    aborts the process.  sp_error_string() names a code.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Compute calls are asynchronous on that stream.  Calls that return sizes to
+ *    the host (create, export, info) synchronise the stream.
+ *  - Device memory for matrices is allocated by the library (stream-ordered)
+ *    and freed by the matching destroy.  Block vectors are either allocated by
+ *    the library (sp_dense_create) or are views of caller memory
+ *    (sp_dense_view), which the library never frees.
+ *  - Block vectors (x, y, z) are always in the caller's original row order;
+ *    the sigma permutation is internal to the matrix.
+ *  - Integer data (row pointers int64, column indices int32, permutation and
+ *    padding) are kept exact.  Matrices need nrows, ncols < 2^31 and at most
+ *    2^31 - 1 nonzeros per row (local indices are 32-bit, Sec. "Sparse matrix
+ *    storage", local vs global indices); stored entries are counted in int64.
+ *  - Thread safety: distinct handles may be used from distinct host threads.
+ *    Calls that use the same matrix handle with dot products requested must be
+ *    ordered (same stream, or synchronised): they share the handle's
+ *    reduction scratch.
+ */
+#ifndef SELLCS_H
+#define SELLCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ errors */
+#define SP_OK 0
+#define SP_ERR_ARG (-1)         /* null pointer, bad flag combination, aliasing */
+#define SP_ERR_DIM (-2)         /* shapes of A, x, y, z disagree */
+#define SP_ERR_DTYPE (-3)       /* unsupported value / vector precision pair */
+#define SP_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define SP_ERR_OOM (-5)         /* device allocation failed */
+#define SP_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up */
+#define SP_ERR_FORMAT (-7)      /* CSR input invalid (row pointers, column range) */
+#define SP_ERR_UNSUPPORTED (-8) /* valid request this build does not implement */
+
+SP_API const char *sp_error_string(int code);
+/* Text of the last CUDA failure seen by this thread (diagnostics only). */
+SP_API const char *sp_last_error_detail(void);
+
+/* ------------------------------------------------------------------ types */
+typedef enum { SP_F64 = 0, SP_F32 = 1, SP_BF16 = 2 } sp_dtype;
+typedef enum { SP_ROW_MAJOR = 0, SP_COL_MAJOR = 1 } sp_layout;
+
+typedef struct sp_mat sp_mat;     /* opaque: SELL-C-sigma matrix on the device */
+typedef struct sp_dense sp_dense; /* opaque: dense block vector (owning or view) */
+
+/* ------------------------------------------------------------------ sparse matrix */
+
+/* Flags of sp_mat_create_csr / sp_mat_update_values. */
+#define SP_MAT_CSR_ON_DEVICE (1u << 0)  /* rowptr, col, val are device pointers (else host) */
+#define SP_MAT_VAL_F32 (1u << 1)        /* val points to float (else double) */
+#define SP_MAT_WITH_TRANSPOSE (1u << 2) /* also build A^T in SELL-C-sigma (needed by sp_spmv_adjoint) */
+
+/*
+ * Build a SELL-C-sigma matrix from CSR (GHOST: "construct a SELL-C-sigma matrix
+ * from raw CRS data, i.e., row pointers, column indices, and values").
+ *   nrows, ncols   matrix shape (nrows >= 0, ncols >= 1 unless nrows == 0)
+ *   rowptr         int64[nrows+1], rowptr[0] = 0, non-decreasing
+ *   col            int32[nnz], each in [0, ncols); any order inside a row (the
+ *                  stored order is the given order)
+ *   val            double[nnz] (float[nnz] with SP_MAT_VAL_F32), rounded once
+ *                  to val_dtype (f64 -> f32 round-to-nearest-even; -> bf16 via
+ *                  f32, both round-to-nearest-even)
+ *   C              chunk height, 1 <= C <= 1024
+ *   sigma          sort window, >= 1 (rows are sorted by length, longest first,
+ *                  stably, inside each window of sigma rows starting at row 0)
+ * The inputs are copied; they may be freed when the call returns.  The call
+ * validates the CSR on the device and returns SP_ERR_FORMAT for a malformed
+ * input (nothing is left allocated).  Synchronises the stream.
+ */
+SP_API int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t *rowptr,
+                      const int32_t *col, const void *val, int C, int64_t sigma, sp_dtype val_dtype,
+                      unsigned flags, void *stream);
+
+/*
+ * Replace the values of A (and of its transpose, if built) keeping the pattern
+ * (GHOST: "each subsequent matrix construction only needs to update the
+ * matrix values").  val is in the CSR order given at creation: double[nnz], or
+ * float[nnz] with SP_MAT_VAL_F32; host unless SP_MAT_CSR_ON_DEVICE.
+ * Asynchronous for device input.
+ */
+SP_API int sp_mat_update_values(sp_mat *A, const void *val, unsigned flags, void *stream);
+
+/* New handle sharing A's pattern (and transpose pattern) with A's values
+ * converted to val_dtype (from A's stored values).  Asynchronous. */
+SP_API int sp_mat_clone_values(sp_mat **out, const sp_mat *A, sp_dtype val_dtype, void *stream);
+
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    int64_t nchunks;  /* ceil(nrows / C) */
+    int64_t nstored;  /* entries stored including padding: sum_c C * chunklen[c] */
+    int32_t C;
+    int32_t maxrowlen;
+    int64_t sigma;
+    sp_dtype val_dtype;
+    int32_t has_transpose;
+} sp_mat_info_t;
+
+SP_API int sp_mat_info(const sp_mat *A, sp_mat_info_t *info);
+
+/*
+ * Copy the SELL-C-sigma arrays to host buffers sized from sp_mat_info (any
+ * pointer may be NULL to skip it):
+ *   chunkptr int64[nchunks+1]  offset of each chunk in col/val
+ *   chunklen int32[nchunks]    padded row length of each chunk
+ *   slotlen  int32[nchunks*C]  real length of the row in each slot (0 = padding row)
+ *   perm     int32[nchunks*C]  original row of each slot (-1 = padding row)
+ *   col      int32[nstored]    column of entry j of slot r of chunk c at chunkptr[c] + j*C + r
+ *   val      double[nstored]   values widened to double (padding entries are 0)
+ * Padding entries carry the column of the last real entry of their row (0 for
+ * an empty or padding row).  Synchronises the stream.
+ */
+SP_API int sp_mat_export_sell(const sp_mat *A, int64_t *chunkptr, int32_t *chunklen, int32_t *slotlen,
+                       int32_t *perm, int32_t *col, double *val, void *stream);
+
+/* Same for the transpose built with SP_MAT_WITH_TRANSPOSE (SP_ERR_ARG if absent). */
+SP_API int sp_mat_export_sell_transpose(const sp_mat *A, int64_t *chunkptr, int32_t *chunklen,
+                                 int32_t *slotlen, int32_t *perm, int32_t *col, double *val,
+                                 void *stream);
+
+/* Rebuild CSR (original row order) on the host: rowptr int64[nrows+1], col int32[nnz],
+ * val double[nnz].  Synchronises the stream. */
+SP_API int sp_mat_to_csr(const sp_mat *A, int64_t *rowptr, int32_t *col, double *val, void *stream);
+
+/* Frees the device arrays (stream-ordered on the given stream). */
+SP_API int sp_mat_destroy(sp_mat *A, void *stream);
+
+/* ------------------------------------------------------------------ dense block vectors */
+
+/*
+ * A dense nrows x ncols block vector (GHOST ghost_densemat).  Row-major =
+ * interleaved vectors, element (i,k) at ptr[i*ld + k]; column-major: ptr[k*ld + i].
+ * dtype SP_F64 or SP_F32.
+ */
+SP_API int sp_dense_create(sp_dense **out, int64_t nrows, int32_t ncols, sp_dtype dtype, sp_layout layout,
+                    void *stream);
+/* View of caller device memory (never freed by the library).  ld >= ncols
+ * (row-major) or ld >= nrows (column-major). */
+SP_API int sp_dense_view(sp_dense **out, void *dev_ptr, int64_t nrows, int32_t ncols, int64_t ld,
+                  sp_dtype dtype, sp_layout layout);
+/* Compact view of columns [col0, col0+ncols) of src (GHOST "compact view"). */
+SP_API int sp_dense_view_cols(sp_dense **out, const sp_dense *src, int32_t col0, int32_t ncols);
+/* Device pointer and shape of a block vector (any output may be NULL). */
+SP_API int sp_dense_data(const sp_dense *d, void **ptr, int64_t *nrows, int32_t *ncols, int64_t *ld,
+                  sp_dtype *dtype, sp_layout *layout);
+/* Frees the memory only if d owns it. */
+SP_API int sp_dense_destroy(sp_dense *d, void *stream);
+
+/* ------------------------------------------------------------------ augmented SpMMV */
+
+/* Augmentation flags (each enables one part; GHOST_SPMV_* in the paper). */
+#define SP_SPMV_SCALE (1u << 0)  /* multiply by alpha (else alpha = 1) */
+#define SP_SPMV_SHIFT (1u << 1)  /* subtract gamma[0] x (one shift for all vectors) */
+#define SP_SPMV_VSHIFT (1u << 2) /* subtract gamma[k] x_k (one shift per vector) */
+#define SP_SPMV_AXPBY (1u << 3)  /* add beta y_old (else y_old is not read) */
+#define SP_SPMV_DOT_YY (1u << 4) /* dot[k]       = <y_k, y_k> (new y) */
+#define SP_SPMV_DOT_XY (1u << 5) /* dot[w + k]   = <x_k, y_k> (new y) */
+#define SP_SPMV_DOT_XX (1u << 6) /* dot[2w + k]  = <x_k, x_k> */
+#define SP_SPMV_CHAIN_AXPBY (1u << 7) /* z = delta z + eta y (new y) */
+#define SP_SPMV_DOT_HOST (1u << 8)    /* dot is a host pointer: the call synchronises */
+#define SP_SPMV_DOT_ANY (SP_SPMV_DOT_YY | SP_SPMV_DOT_XY | SP_SPMV_DOT_XX)
+
+#define SP_MAX_VSHIFT 1024 /* widest block with per-vector shifts */
+
+typedef struct {
+    uint32_t flags;
+    double alpha, beta, delta, eta;
+    const double *gamma; /* host: 1 value (SHIFT) or ncols(x) values (VSHIFT) */
+    sp_dense *z;         /* CHAIN_AXPBY target, same shape as y */
+    double *dot;         /* 3*w doubles [yy | xy | xx]; only requested slots are written */
+} sp_spmv_opts;
+
+#define SP_SPMV_OPTS_INIT {0u, 1.0, 0.0, 0.0, 1.0, NULL, NULL, NULL}
+
+/*
+ * y = alpha (A - gamma I) x + beta y with the requested augmentations
+ * (GHOST ghost_spmv(y, A, x, opts)).
+ *   x   ncols(A) x w, y (and z) nrows(A) x w; same dtype; row- or column-major
+ *   Precision pairs (values / vectors): f64/f64 (f64 accumulation);
+ *   f32/f64, bf16/f64, f32/f32, bf16/f32 (f32 accumulation of the row sums;
+ *   the epilogue runs in the vector precision).  Dot products are always
+ *   accumulated and returned in double.
+ *   SHIFT, VSHIFT, DOT_XY and DOT_XX need a square A.  SHIFT and VSHIFT are
+ *   exclusive.  x must not overlap y or z, and z must not overlap y
+ *   (SP_ERR_ARG).  The reductions are deterministic (fixed order).
+ */
+SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts *opts, void *stream);
+
+/* ------------------------------------------------------------------ derivatives */
+
+/*
+ * Adjoint of y = A x for a row-major g = dL/dy (nrows x w):
+ *   dx    = A^T g            (ncols x w; needs SP_MAT_WITH_TRANSPOSE; NULL to skip)
+ *   dvals[p] = sum_k g[row(p),k] x[col(p),k] for every nonzero p, in the CSR
+ *           order given at creation (device array of nnz elements in the
+ *           precision of x and g; NULL to skip).
+ * x, g and dx share one dtype (f64 or f32) and are row-major.  Asynchronous.
+ */
+SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
+                    void *stream);
+
+/* ------------------------------------------------------------------ device info */
+/* Streaming multiprocessor count of the current device (for grid sizing tests). */
+SP_API int sp_device_sm_count(int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SELLCS_H */

@@ -1,0 +1,135 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+
+#include "../../include/sellcs.h"
+
+#define SP_TRY(expr)                      \
+    do {                                  \
+        int _e = (expr);                  \
+        if (_e != SP_OK) return _e;       \
+    } while (0)
+
+#define SP_CUDA(expr)                                                     \
+    do {                                                                  \
+        cudaError_t _c = (expr);                                          \
+        if (_c != cudaSuccess) {                                          \
+            sp_internal_note_cuda_error(_c, #expr, __FILE__, __LINE__);   \
+            return _c == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA; \
+        }                                                                 \
+    } while (0)
+
+void sp_internal_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+namespace sp {
+
+// ------------------------------------------------------------------ device buffers
+
+// Stream-ordered device allocation owned by a shared_ptr so that patterns can
+// be shared between a matrix and its value clones.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    ~DevBuf();
+};
+using DevBufPtr = std::shared_ptr<DevBuf>;
+int dev_alloc(DevBufPtr &out, size_t bytes, cudaStream_t s);
+
+// SELL-C-sigma pattern: everything except the values.
+struct Pattern {
+    int64_t nrows = 0, ncols = 0, nnz = 0;
+    int64_t nchunks = 0, nslots = 0, nstored = 0;
+    int32_t C = 1;
+    int64_t sigma = 1;
+    int32_t maxrowlen = 0;
+    DevBufPtr chunkptr;  // int64[nchunks+1]
+    DevBufPtr chunklen;  // int32[nchunks]
+    DevBufPtr slotlen;   // int32[nslots]
+    DevBufPtr perm;      // int32[nslots], -1 for padding rows
+    DevBufPtr col;       // int32[nstored]
+    DevBufPtr rowptr;    // int64[nrows+1], the CSR row pointers (original order)
+    // for the transpose only: position in the parent's CSR of each of its own CSR entries
+    DevBufPtr src_index; // int64[nnz]
+};
+using PatternPtr = std::shared_ptr<Pattern>;
+
+}  // namespace sp
+
+struct sp_mat {
+    sp::PatternPtr pat;
+    sp_dtype vdt = SP_F64;
+    sp::DevBufPtr val;           // vdt[nstored]
+    sp_mat *transpose = nullptr; // owned
+    // reduction scratch for the fused dot products (per-block partials + ticket)
+    sp::DevBufPtr scratch;
+    size_t scratch_bytes = 0;
+};
+
+struct sp_dense {
+    void *ptr = nullptr;
+    int64_t nrows = 0;
+    int32_t ncols = 0;
+    int64_t ld = 0;
+    sp_dtype dtype = SP_F64;
+    sp_layout layout = SP_ROW_MAJOR;
+    sp::DevBufPtr owner;  // set when the library allocated the memory
+};
+
+namespace sp {
+
+inline size_t dtype_size(sp_dtype t) { return t == SP_F64 ? 8 : (t == SP_F32 ? 4 : 2); }
+
+inline int ilog2_exact(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return (int64_t(1) << l) == v ? l : -1;
+}
+
+// ------------------------------------------------------------------ conversion entry points
+int build_pattern_and_values(sp_mat *A, int64_t nrows, int64_t ncols, const int64_t *d_rowptr,
+                             const int32_t *d_col, const void *d_val, bool val_f32, int C,
+                             int64_t sigma, cudaStream_t s);
+int build_transpose(sp_mat *A, const int64_t *d_rowptr, const int32_t *d_col, const void *d_val,
+                    bool val_f32, cudaStream_t s);
+int fill_values_from_csr(const Pattern &P, sp_dtype vdt, void *val_sell, const void *d_val_csr,
+                         bool val_f32, cudaStream_t s);
+int gather_values(const void *src, bool src_f32, const int64_t *index, int64_t n, void *dst,
+                  bool dst_f32, cudaStream_t s);
+int convert_values(const void *src, sp_dtype sdt, void *dst, sp_dtype ddt, int64_t n, cudaStream_t s);
+int widen_values(const void *src, sp_dtype sdt, double *dst, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------------ SpMMV launch
+struct VecDesc {
+    const void *ptr;
+    int64_t rs, cs;  // element strides: (i,k) at ptr[i*rs + k*cs]
+};
+
+struct SpmvLaunch {
+    const Pattern *P;
+    const void *val;
+    sp_dtype vdt, xdt;
+    int w;
+    VecDesc x, y, z;
+    uint32_t flags;
+    double alpha, beta, delta, eta;
+    const double *gamma;  // host, w values (already expanded) or null
+    double *dot;          // device, written at dot[q*dot_stride + dot_off + k]
+    int dot_stride, dot_off;
+    double *partials;     // device scratch
+    unsigned *ticket;     // device scratch (zero between calls)
+    int max_blocks;
+};
+int launch_spmv(const SpmvLaunch &L, cudaStream_t s);
+int spmv_scratch_need(int sm_count, size_t *bytes, int *max_blocks);
+
+int launch_sampled(const Pattern &P, sp_dtype xdt, int w, const void *x, const void *g, void *dvals,
+                   cudaStream_t s);
+
+int device_sm_count(int *n);
+
+}  // namespace sp

@@ -1,0 +1,353 @@
+// The augmented SELL-C-sigma SpMMV kernel (GHOST, Sec. "Kernel fusion"):
+//
+//     y = alpha (A - gamma I) x + beta y,  <y,y>, <x,y>, <x,x>,  z = delta z + eta y
+//
+// in one pass over the matrix.
+//
+// Mapping.  A block vector of width w (row-major, "interleaved", which the
+// paper finds faster than column-major, Sec. "Block vectors") is padded to
+// WP = next power of two <= 32.  Each lane owns CPL consecutive columns
+// (a 16-byte vector of x when possible) and G = WP / CPL lanes share one row,
+// so a warp covers R = 32 / G rows.  For w = 1 that is one row per lane: with
+// C = 32 a warp reads 32 consecutive values and 32 consecutive column indices
+// of a chunk column per step -- the coalescing the SELL layout was designed for
+// (chunk entries stored column-wise).  For wider blocks the G lanes of a row
+// read its x row as whole 16-byte vectors, so every gathered x row is one
+// contiguous 8*w- or 4*w-byte line.
+//
+// Matrix values and indices are read once, with the streaming (evict-first)
+// cache hint; x goes through the read-only path so that its reuse stays in L1
+// and L2.  Each row runs only to its own length (the per-slot length), so
+// padding is never read or multiplied.
+//
+// The grid is persistent (at most SMs x resident blocks) and walks the rows
+// in a block-strided loop.  Dot products are reduced in a fixed order: lanes
+// of a warp by xor shuffles, warps of a block through shared memory, blocks by
+// the last block to finish (per-block partials + an atomic ticket), so the
+// result is deterministic and no block ever waits for another.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace sp {
+
+constexpr int kSpmvThreads = 256;
+constexpr int kSpmvWarps = kSpmvThreads / 32;
+constexpr int kMaxTileW = 32;
+
+struct SpmvArgs {
+    const void *val;
+    const int32_t *col;
+    const int64_t *chunkptr;
+    const int32_t *slotlen;
+    const int32_t *perm;  // null: identity (sigma = 1)
+    int64_t nrows;
+    int64_t nslots;
+    int32_t C;
+    int32_t w;
+    const void *x;
+    int64_t xrs, xcs;
+    void *y;
+    int64_t yrs, ycs;
+    void *z;
+    int64_t zrs, zcs;
+    uint32_t flags;
+    double alpha, beta, delta, eta;
+    double *dot;
+    int32_t dot_stride, dot_off;
+    double *partials;
+    unsigned *ticket;
+    double gamma[kMaxTileW];
+};
+
+template <class VT, class XT>
+struct AccOf { using T = float; };
+template <>
+struct AccOf<double, double> { using T = double; };
+
+template <class XT, int WP>
+__host__ __device__ constexpr int cols_per_lane() {
+    return (int)(16 / sizeof(XT)) * 2 < WP ? (int)(16 / sizeof(XT)) * 2 : WP;
+}
+
+// Host mirror of cols_per_lane for a runtime width.
+inline int host_cols_per_lane(size_t xsize, int w) {
+    int wp = 1;
+    while (wp < w) wp <<= 1;
+    int c = (int)(16 / xsize) * 2;
+    return c < wp ? c : wp;
+}
+
+template <class AT, class VT>
+__device__ __forceinline__ AT val_to_acc(VT v) { return (AT)v; }
+template <>
+__device__ __forceinline__ float val_to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+template <class T>
+__device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+// Load CPL consecutive columns of one row of a block vector.
+// VEC: all CPL columns valid, unit column stride, address aligned to
+// min(16, CPL*sizeof(XT)) bytes.
+template <class XT, int CPL, bool VEC>
+__device__ __forceinline__ void load_cols(const XT *__restrict__ p, int64_t cs, int nvalid, XT (&o)[CPL]) {
+    if constexpr (VEC) {
+        constexpr int B = CPL * (int)sizeof(XT);
+        if constexpr (B % 16 == 0) {
+#pragma unroll
+            for (int q = 0; q < B / 16; ++q) {
+                uint4 u = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+                memcpy(&o[q * (16 / sizeof(XT))], &u, 16);
+            }
+        } else if constexpr (B == 8) {
+            uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+            memcpy(&o[0], &u, 8);
+        } else {
+            o[0] = __ldg(p);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) o[c] = c < nvalid ? __ldg(p + c * cs) : XT(0);
+    }
+}
+
+// Plain (coherent) load/store of an output row: y and z are read and written.
+template <class XT, int CPL, bool VEC>
+__device__ __forceinline__ void load_out(const XT *p, int64_t cs, int nvalid, XT (&o)[CPL]) {
+    if constexpr (VEC) {
+        constexpr int B = CPL * (int)sizeof(XT);
+        if constexpr (B % 16 == 0) {
+#pragma unroll
+            for (int q = 0; q < B / 16; ++q) {
+                uint4 u = reinterpret_cast<const uint4 *>(p)[q];
+                memcpy(&o[q * (16 / sizeof(XT))], &u, 16);
+            }
+        } else if constexpr (B == 8) {
+            uint2 u = *reinterpret_cast<const uint2 *>(p);
+            memcpy(&o[0], &u, 8);
+        } else {
+            o[0] = *p;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) o[c] = c < nvalid ? p[c * cs] : XT(0);
+    }
+}
+
+template <class XT, int CPL, bool VEC>
+__device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const XT (&o)[CPL]) {
+    if constexpr (VEC) {
+        constexpr int B = CPL * (int)sizeof(XT);
+        if constexpr (B % 16 == 0) {
+#pragma unroll
+            for (int q = 0; q < B / 16; ++q) {
+                uint4 u;
+                memcpy(&u, &o[q * (16 / sizeof(XT))], 16);
+                reinterpret_cast<uint4 *>(p)[q] = u;
+            }
+        } else if constexpr (B == 8) {
+            uint2 u;
+            memcpy(&u, &o[0], 8);
+            *reinterpret_cast<uint2 *>(p) = u;
+        } else {
+            *p = o[0];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if (c < nvalid) p[c * cs] = o[c];
+    }
+}
+
+// Row sums t[c] = sum_j val(s,j) * x[col(s,j), k0 + c] for the row in one slot.
+template <class VT, class XT, class AT, int CPL, bool VEC, int U>
+__device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
+                                            int len, const XT *__restrict__ xk, int64_t xrs, int64_t xcs,
+                                            int nvalid, AT (&acc)[CPL]) {
+    int j = 0;
+    for (; j + U <= len; j += U) {
+        int32_t cc[U];
+        VT vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = ld_stream(cp + (int64_t)u * C);
+            vv[u] = ld_stream(vp + (int64_t)u * C);
+        }
+        vp += (int64_t)U * C;
+        cp += (int64_t)U * C;
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                XT xv[CPL];
+                load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+                AT v = val_to_acc<AT, VT>(vv[u]);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+            }
+        }
+    }
+    for (; j < len; ++j) {
+        int32_t cc = ld_stream(cp);
+        VT vv = ld_stream(vp);
+        vp += C;
+        cp += C;
+        if (nvalid > 0) {
+            XT xv[CPL];
+            load_cols<XT, CPL, VEC>(xk + (int64_t)cc * xrs, xcs, nvalid, xv);
+            AT v = val_to_acc<AT, VT>(vv);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+        }
+    }
+}
+
+// Final step of the fused reductions: per-block partial sums, and the last
+// block to arrive adds them up in block order.
+template <int CPL, int G>
+__device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&dyy)[CPL], double (&dxy)[CPL],
+                                            double (&dxx)[CPL]) {
+    __shared__ double sred[kSpmvWarps][3][kMaxTileW];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
+            dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
+            dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
+        }
+    }
+    if (lane < G) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            int k = k0 + c;
+            if (k < a.w) {
+                sred[warp][0][k] = dyy[c];
+                sred[warp][1][k] = dxy[c];
+                sred[warp][2][k] = dxx[c];
+            }
+        }
+    }
+    __syncthreads();
+    const int nv = 3 * a.w;
+    const int nb = gridDim.x;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        int q = t / a.w, k = t - q * a.w;
+        double s = 0.0;
+#pragma unroll
+        for (int wi = 0; wi < kSpmvWarps; ++wi) s += sred[wi][q][k];
+        a.partials[(int64_t)t * nb + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(a.ticket, 1u) == (unsigned)nb - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int t = warp; t < nv; t += kSpmvWarps) {
+        int q = t / a.w, k = t - q * a.w;
+        if (!(a.flags & (SP_SPMV_DOT_YY << q))) continue;
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += __ldcg(a.partials + (int64_t)t * nb + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) a.dot[(int64_t)q * a.dot_stride + a.dot_off + k] = s;
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+template <class VT, class XT, int WP, bool VEC>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ SpmvArgs a) {
+    using AT = typename AccOf<VT, XT>::T;
+    constexpr int CPL = cols_per_lane<XT, WP>();
+    constexpr int G = WP / CPL;
+    constexpr int R = 32 / G;
+    constexpr int ROWS = R * kSpmvWarps;
+    constexpr int U = CPL >= 4 ? 2 : 4;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, rw = lane / G;
+    const int k0 = gl * CPL;
+    const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
+    const uint32_t f = a.flags;
+    const bool dots = (f & SP_SPMV_DOT_ANY) != 0;
+    const bool shift = (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0;
+    const bool need_xi = shift || (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX));
+    const VT *__restrict__ val = (const VT *)a.val;
+    const XT *__restrict__ x = (const XT *)a.x;
+    XT *y = (XT *)a.y;
+    XT *z = (XT *)a.z;
+    const XT alpha = (XT)a.alpha, beta = (XT)a.beta, delta = (XT)a.delta, eta = (XT)a.eta;
+    XT gam[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) gam[c] = (shift && k0 + c < a.w) ? (XT)a.gamma[k0 + c] : XT(0);
+
+    double dyy[CPL], dxy[CPL], dxx[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) dyy[c] = dxy[c] = dxx[c] = 0.0;
+
+    const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
+    for (int64_t base = (int64_t)blockIdx.x * ROWS; base < a.nslots; base += (int64_t)gridDim.x * ROWS) {
+        const int64_t s = base + warp * R + rw;
+        if (s >= a.nslots) continue;
+        const int64_t i = a.perm ? (int64_t)a.perm[s] : (s < a.nrows ? s : -1);
+        if (i < 0) continue;
+        const uint32_t cidx = (uint32_t)s / (uint32_t)a.C;
+        const int r = (int)((uint32_t)s - cidx * (uint32_t)a.C);
+        const int64_t off = a.chunkptr[cidx] + r;
+        const int len = a.slotlen[s];
+        AT acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+        row_product<VT, XT, AT, CPL, VEC, U>(val + off, a.col + off, a.C, len, xk, a.xrs, a.xcs, nvalid, acc);
+        if (nvalid <= 0) continue;
+
+        // epilogue: y = alpha (t - gamma x_i) + beta y_i, dots, chain
+        XT xi[CPL], yo[CPL], t[CPL];
+        if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
+        XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
+        if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            XT v = (XT)acc[c];
+            if (shift) v = v - gam[c] * xi[c];
+            if (f & SP_SPMV_SCALE) v = alpha * v;
+            if (f & SP_SPMV_AXPBY) v = v + beta * yo[c];
+            t[c] = v;
+        }
+        store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
+        if (dots) {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                if (c < nvalid) {
+                    double td = (double)t[c], xd = need_xi ? (double)xi[c] : 0.0;
+                    dyy[c] += td * td;
+                    dxy[c] += xd * td;
+                    dxx[c] += xd * xd;
+                }
+            }
+        }
+        if (f & SP_SPMV_CHAIN_AXPBY) {
+            XT zo[CPL];
+            XT *zp = z + i * a.zrs + (int64_t)k0 * a.zcs;
+            load_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) zo[c] = delta * zo[c] + eta * t[c];
+            store_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
+        }
+    }
+    if (dots) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);
+}
+
+// Host-side dispatch over the block width for one (value, vector) type pair.
+template <class VT, class XT>
+int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
+
+}  // namespace sp

@@ -1,0 +1,58 @@
+// Width dispatch for the SpMMV kernel; included by the per-precision
+// translation units (spmv_f64.cu, spmv_f32.cu, spmv_bf16.cu), which compile in
+// parallel.  The block width is a compile-time constant of each kernel
+// variant (the paper's fixed-loop-length code generation, Sec.
+// "Implementation"), padded to a power of two; a variant exists for every
+// width up to 32, so every width is served (the paper's always-correct
+// fallback chain); wider blocks are processed in tiles of 32 columns.
+#pragma once
+
+#include "spmv_kernel.cuh"
+
+namespace sp {
+
+template <class VT, class XT, int WP, bool VEC>
+static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
+    constexpr int CPL = cols_per_lane<XT, WP>();
+    constexpr int G = WP / CPL;
+    constexpr int ROWS = (32 / G) * kSpmvWarps;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC>,
+                                                                      kSpmvThreads, 0);
+        if (e != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+    }
+    int sms = 1;
+    SP_TRY(device_sm_count(&sms));
+    int64_t need = (a.nslots + ROWS - 1) / ROWS;
+    int64_t grid = (int64_t)sms * occ;
+    if (grid > max_blocks) grid = max_blocks;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_spmmv<VT, XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(a);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+template <class VT, class XT, int WP>
+static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+    return vec ? launch_spmv_variant<VT, XT, WP, true>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false>(a, max_blocks, s);
+}
+
+template <class VT, class XT>
+int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+    int w = a.w;
+    if (w <= 1) return launch_spmv_w<VT, XT, 1>(a, vec, max_blocks, s);
+    if (w <= 2) return launch_spmv_w<VT, XT, 2>(a, vec, max_blocks, s);
+    if (w <= 4) return launch_spmv_w<VT, XT, 4>(a, vec, max_blocks, s);
+    if (w <= 8) return launch_spmv_w<VT, XT, 8>(a, vec, max_blocks, s);
+    if (w <= 16) return launch_spmv_w<VT, XT, 16>(a, vec, max_blocks, s);
+    if (w <= 32) return launch_spmv_w<VT, XT, 32>(a, vec, max_blocks, s);
+    return SP_ERR_ARG;
+}
+
+}  // namespace sp

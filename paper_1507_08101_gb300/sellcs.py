@@ -1,0 +1,392 @@
+"""ctypes binding of the C ABI in ``include/sellcs.h``.
+
+Argument marshalling only: every step of the product runs in the CUDA
+library.  Functions carry the C names (``sp_mat_create_csr``, ``sp_spmv``,
+...); :class:`SellMatrix` and :func:`spmv` wrap them for torch tensors, whose
+device memory and current stream are passed through as raw pointers.  If the
+library has not been built the import of this module still works, but the
+first call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# ------------------------------------------------------------------ constants (mirror of sellcs.h)
+SP_OK = 0
+SP_ERR_ARG, SP_ERR_DIM, SP_ERR_DTYPE, SP_ERR_CUDA, SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_FORMAT, \
+    SP_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
+SP_F64, SP_F32, SP_BF16 = 0, 1, 2
+SP_ROW_MAJOR, SP_COL_MAJOR = 0, 1
+SP_MAT_CSR_ON_DEVICE, SP_MAT_VAL_F32, SP_MAT_WITH_TRANSPOSE = 1, 2, 4
+SP_SPMV_SCALE = 1 << 0
+SP_SPMV_SHIFT = 1 << 1
+SP_SPMV_VSHIFT = 1 << 2
+SP_SPMV_AXPBY = 1 << 3
+SP_SPMV_DOT_YY = 1 << 4
+SP_SPMV_DOT_XY = 1 << 5
+SP_SPMV_DOT_XX = 1 << 6
+SP_SPMV_CHAIN_AXPBY = 1 << 7
+SP_SPMV_DOT_HOST = 1 << 8
+SP_SPMV_DOT_ANY = SP_SPMV_DOT_YY | SP_SPMV_DOT_XY | SP_SPMV_DOT_XX
+
+DTYPES = {"f64": SP_F64, "f32": SP_F32, "bf16": SP_BF16}
+
+
+class sp_mat_info_t(ct.Structure):
+    _fields_ = [("nrows", ct.c_int64), ("ncols", ct.c_int64), ("nnz", ct.c_int64), ("nchunks", ct.c_int64),
+                ("nstored", ct.c_int64), ("C", ct.c_int32), ("maxrowlen", ct.c_int32), ("sigma", ct.c_int64),
+                ("val_dtype", ct.c_int), ("has_transpose", ct.c_int32)]
+
+
+class sp_spmv_opts(ct.Structure):
+    _fields_ = [("flags", ct.c_uint32), ("alpha", ct.c_double), ("beta", ct.c_double), ("delta", ct.c_double),
+                ("eta", ct.c_double), ("gamma", ct.POINTER(ct.c_double)), ("z", ct.c_void_p),
+                ("dot", ct.c_void_p)]
+
+
+class SpError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {sp_error_string(code)} ({code}) {sp_last_error_detail()}")
+
+
+_lib = None
+P = ct.c_void_p
+PP = ct.POINTER(ct.c_void_p)
+I = ct.c_int
+I32 = ct.c_int32
+I64 = ct.c_int64
+U = ct.c_uint
+
+_SIGS = {
+    "sp_error_string": (ct.c_char_p, [I]),
+    "sp_last_error_detail": (ct.c_char_p, []),
+    "sp_device_sm_count": (I, [ct.POINTER(I)]),
+    "sp_mat_create_csr": (I, [PP, I64, I64, P, P, P, I, I64, I, U, P]),
+    "sp_mat_update_values": (I, [P, P, U, P]),
+    "sp_mat_clone_values": (I, [PP, P, I, P]),
+    "sp_mat_info": (I, [P, ct.POINTER(sp_mat_info_t)]),
+    "sp_mat_export_sell": (I, [P, P, P, P, P, P, P, P]),
+    "sp_mat_export_sell_transpose": (I, [P, P, P, P, P, P, P, P]),
+    "sp_mat_to_csr": (I, [P, P, P, P, P]),
+    "sp_mat_destroy": (I, [P, P]),
+    "sp_dense_create": (I, [PP, I64, I32, I, I, P]),
+    "sp_dense_view": (I, [PP, P, I64, I32, I64, I, I]),
+    "sp_dense_view_cols": (I, [PP, P, I32, I32]),
+    "sp_dense_data": (I, [P, PP, ct.POINTER(I64), ct.POINTER(I32), ct.POINTER(I64), ct.POINTER(I), ct.POINTER(I)]),
+    "sp_dense_destroy": (I, [P, P]),
+    "sp_spmv": (I, [P, P, P, ct.POINTER(sp_spmv_opts), P]),
+    "sp_spmv_adjoint": (I, [P, P, P, P, P, P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run paper_1507_08101_gb300.build.build()")
+        L = ct.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def sp_error_string(code: int) -> str:
+    return lib().sp_error_string(code).decode()
+
+
+def sp_last_error_detail() -> str:
+    return lib().sp_last_error_detail().decode()
+
+
+def check(rc: int, what: str):
+    if rc != SP_OK:
+        raise SpError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ct.c_void_p)
+    return ct.c_void_p(a.data_ptr())
+
+
+# ------------------------------------------------------------------ raw names
+
+
+def sp_mat_create_csr(nrows, ncols, rowptr, col, val, C, sigma, val_dtype, flags, stream=None):
+    h = ct.c_void_p()
+    check(lib().sp_mat_create_csr(ct.byref(h), nrows, ncols, _ptr(rowptr), _ptr(col), _ptr(val), C, sigma,
+                                  val_dtype, flags, _stream(stream)), "sp_mat_create_csr")
+    return h
+
+
+def sp_dense_view(t, layout=SP_ROW_MAJOR):
+    """View of a 1-D or 2-D CUDA tensor (float64/float32), row-major by default.
+
+    A column-major view of an (n, w) tensor expects its transposed strides
+    (t.t() contiguous)."""
+    import torch
+    if t.dim() == 1:
+        n, w, ld = t.shape[0], 1, 1
+        if layout == SP_COL_MAJOR:
+            ld = n
+    elif layout == SP_ROW_MAJOR:
+        n, w = t.shape
+        assert t.stride(1) == 1, "row-major view needs unit column stride"
+        ld = t.stride(0) if n > 1 else w
+    else:
+        n, w = t.shape
+        assert t.stride(0) == 1, "column-major view needs unit row stride"
+        ld = t.stride(1) if w > 1 else n
+    dt = {torch.float64: SP_F64, torch.float32: SP_F32}[t.dtype]
+    h = ct.c_void_p()
+    check(lib().sp_dense_view(ct.byref(h), _ptr(t), n, w, max(ld, 1), dt, layout), "sp_dense_view")
+    return h
+
+
+def sp_dense_destroy(h, stream=None):
+    check(lib().sp_dense_destroy(h, _stream(stream)), "sp_dense_destroy")
+
+
+def sp_device_sm_count():
+    n = ct.c_int()
+    check(lib().sp_device_sm_count(ct.byref(n)), "sp_device_sm_count")
+    return n.value
+
+
+# ------------------------------------------------------------------ matrix wrapper
+
+
+class SellMatrix:
+    """Owning handle of a SELL-C-sigma matrix built from CSR arrays.
+
+    ``csr`` is any object with nrows, ncols, rowptr, col, val (host numpy), or
+    a tuple (nrows, ncols, rowptr, col, val) of CUDA tensors (then the CSR is
+    read on the device)."""
+
+    def __init__(self, csr, C=32, sigma=1, dtype="f64", with_transpose=False, stream=None):
+        import torch
+        self._lib = lib()
+        flags = SP_MAT_WITH_TRANSPOSE if with_transpose else 0
+        if isinstance(csr, tuple):
+            nrows, ncols, rowptr, col, val = csr
+            flags |= SP_MAT_CSR_ON_DEVICE
+            if val.dtype == torch.float32:
+                flags |= SP_MAT_VAL_F32
+            keep = (rowptr, col, val)
+        else:
+            nrows, ncols = csr.nrows, csr.ncols
+            rowptr = np.ascontiguousarray(csr.rowptr, np.int64)
+            col = np.ascontiguousarray(csr.col, np.int32)
+            val = np.ascontiguousarray(csr.val)
+            if val.dtype == np.float32:
+                flags |= SP_MAT_VAL_F32
+            else:
+                val = val.astype(np.float64, copy=False)
+            keep = (rowptr, col, val)
+        self.handle = sp_mat_create_csr(nrows, ncols, keep[0], keep[1], keep[2], C, sigma, DTYPES[dtype], flags,
+                                        stream)
+        self.dtype = dtype
+
+    @classmethod
+    def _from_handle(cls, h, dtype):
+        obj = cls.__new__(cls)
+        obj._lib = lib()
+        obj.handle = h
+        obj.dtype = dtype
+        return obj
+
+    def info(self) -> dict:
+        inf = sp_mat_info_t()
+        check(self._lib.sp_mat_info(self.handle, ct.byref(inf)), "sp_mat_info")
+        return {f: getattr(inf, f) for f, _ in sp_mat_info_t._fields_}
+
+    @property
+    def shape(self):
+        i = self.info()
+        return i["nrows"], i["ncols"]
+
+    def export_sell(self, transpose=False, stream=None) -> dict:
+        i = self.info()
+        if transpose:
+            i = self.transpose_info()
+        nch, C, nst = i["nchunks"], i["C"], i["nstored"]
+        out = dict(chunkptr=np.empty(nch + 1, np.int64), chunklen=np.empty(nch, np.int32),
+                   slotlen=np.empty(nch * C, np.int32), perm=np.empty(nch * C, np.int32),
+                   col=np.empty(nst, np.int32), val=np.empty(nst, np.float64))
+        fn = self._lib.sp_mat_export_sell_transpose if transpose else self._lib.sp_mat_export_sell
+        check(fn(self.handle, *[_ptr(out[k]) for k in ("chunkptr", "chunklen", "slotlen", "perm", "col", "val")],
+                 _stream(stream)), "sp_mat_export_sell")
+        return out
+
+    def transpose_info(self) -> dict:
+        i = self.info()
+        assert i["has_transpose"]
+        e = dict(nrows=i["ncols"], ncols=i["nrows"], C=i["C"])
+        # sizes of the transpose come from its own export; compute from a dry export of chunk counts
+        nch = (e["nrows"] + e["C"] - 1) // e["C"]
+        cp = np.empty(nch + 1, np.int64)
+        check(self._lib.sp_mat_export_sell_transpose(self.handle, _ptr(cp), None, None, None, None, None,
+                                                     _stream(None)), "sp_mat_export_sell_transpose")
+        e.update(nchunks=nch, nstored=int(cp[-1]))
+        return e
+
+    def to_csr(self, stream=None):
+        i = self.info()
+        rp = np.empty(i["nrows"] + 1, np.int64)
+        col = np.empty(i["nnz"], np.int32)
+        val = np.empty(i["nnz"], np.float64)
+        check(self._lib.sp_mat_to_csr(self.handle, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)),
+              "sp_mat_to_csr")
+        return rp, col, val
+
+    def update_values(self, val, stream=None):
+        import torch
+        flags = 0
+        if isinstance(val, torch.Tensor):
+            assert val.is_cuda and val.is_contiguous()
+            flags |= SP_MAT_CSR_ON_DEVICE
+            if val.dtype == torch.float32:
+                flags |= SP_MAT_VAL_F32
+            else:
+                assert val.dtype == torch.float64
+        else:
+            val = np.ascontiguousarray(val)
+            if val.dtype == np.float32:
+                flags |= SP_MAT_VAL_F32
+            else:
+                val = val.astype(np.float64, copy=False)
+        check(self._lib.sp_mat_update_values(self.handle, _ptr(val), flags, _stream(stream)),
+              "sp_mat_update_values")
+
+    def clone(self, dtype: str, stream=None) -> "SellMatrix":
+        h = ct.c_void_p()
+        check(self._lib.sp_mat_clone_values(ct.byref(h), self.handle, DTYPES[dtype], _stream(stream)),
+              "sp_mat_clone_values")
+        return SellMatrix._from_handle(h, dtype)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sp_mat_destroy(self.handle, _stream(None))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ product
+
+
+def make_opts(w, *, alpha=None, gamma=None, beta=None, dot_yy=False, dot_xy=False, dot_xx=False, z_handle=None,
+              delta=None, eta=None, dot_ptr=None, dot_host=False):
+    o = sp_spmv_opts()
+    f = 0
+    o.alpha, o.beta, o.delta, o.eta = 1.0, 0.0, 0.0, 1.0
+    keep = []
+    if alpha is not None:
+        f |= SP_SPMV_SCALE
+        o.alpha = float(alpha)
+    if gamma is not None:
+        g = np.atleast_1d(np.asarray(gamma, np.float64))
+        if g.size == 1 and w != 1:
+            f |= SP_SPMV_SHIFT
+        elif g.size == 1:
+            f |= SP_SPMV_SHIFT
+        else:
+            assert g.size == w
+            f |= SP_SPMV_VSHIFT
+        g = np.ascontiguousarray(g)
+        keep.append(g)
+        o.gamma = g.ctypes.data_as(ct.POINTER(ct.c_double))
+    if beta is not None:
+        f |= SP_SPMV_AXPBY
+        o.beta = float(beta)
+    if dot_yy:
+        f |= SP_SPMV_DOT_YY
+    if dot_xy:
+        f |= SP_SPMV_DOT_XY
+    if dot_xx:
+        f |= SP_SPMV_DOT_XX
+    if z_handle is not None:
+        f |= SP_SPMV_CHAIN_AXPBY
+        o.z = z_handle
+        o.delta = float(delta)
+        o.eta = float(eta)
+    if dot_host:
+        f |= SP_SPMV_DOT_HOST
+    o.flags = f
+    o.dot = dot_ptr
+    return o, keep
+
+
+def spmv(A: SellMatrix, x, y, *, alpha=None, gamma=None, beta=None, dot_yy=False, dot_xy=False, dot_xx=False,
+         z=None, delta=None, eta=None, dot=None, layout=SP_ROW_MAJOR, stream=None):
+    """y = alpha (A - gamma I) x + beta y (+ dots into ``dot``, + z = delta z + eta y).
+
+    x, y, z: CUDA tensors (n,) or (n, w); dot: CUDA float64 tensor of 3*w
+    (written at [yy | xy | xx]).  Returns ``dot``."""
+    L = lib()
+    hx = sp_dense_view(x, layout)
+    hy = sp_dense_view(y, layout)
+    hz = sp_dense_view(z, layout) if z is not None else None
+    w = 1 if x.dim() == 1 else x.shape[1]
+    try:
+        if (dot_yy or dot_xy or dot_xx) and dot is None:
+            import torch
+            dot = torch.full((3 * w,), float("nan"), dtype=torch.float64, device=x.device)
+        o, keep = make_opts(w, alpha=alpha, gamma=gamma, beta=beta, dot_yy=dot_yy, dot_xy=dot_xy, dot_xx=dot_xx,
+                            z_handle=hz, delta=delta, eta=eta, dot_ptr=_ptr(dot) if dot is not None else None)
+        check(L.sp_spmv(hy, A.handle, hx, ct.byref(o), _stream(stream)), "sp_spmv")
+    finally:
+        L.sp_dense_destroy(hx, None)
+        L.sp_dense_destroy(hy, None)
+        if hz is not None:
+            L.sp_dense_destroy(hz, None)
+    return dot
+
+
+def spmv_adjoint(A: SellMatrix, g, x=None, dx=None, dvals=None, stream=None):
+    """dx = A^T g (into ``dx``) and dvals[p] = sum_k g[row p] x[col p] (into ``dvals``)."""
+    L = lib()
+    hg = sp_dense_view(g)
+    hx = sp_dense_view(x) if x is not None else None
+    hdx = sp_dense_view(dx) if dx is not None else None
+    try:
+        check(L.sp_spmv_adjoint(hdx, _ptr(dvals) if dvals is not None else None, A.handle, hx, hg,
+                                _stream(stream)), "sp_spmv_adjoint")
+    finally:
+        for h in (hg, hx, hdx):
+            if h is not None:
+                L.sp_dense_destroy(h, None)

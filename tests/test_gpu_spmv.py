@@ -1,0 +1,171 @@
+"""GPU parity of the augmented SpMMV (through the C ABI) against the oracle.
+
+Covers every subset of the augmentation flags, block widths 1..33 (padded
+power-of-two variants, the masked generic path and the 32-column tiling),
+chunk heights and sort windows, all five precision pairs, row- and
+column-major block vectors with padded leading dimensions, rectangular
+matrices and the degenerate shapes (empty matrix, empty rows, one row, fewer
+rows than C, a row far longer than the rest)."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1507_08101_gb300 import sellcs
+from tests.gpu_helpers import run_case, to_dev
+from tests.test_oracle_format import random_csr
+from workloads import generators as gen
+
+pytestmark = pytest.mark.gpu
+
+FLAGS = ["scale", "shift", "vshift", "axpby", "dot_yy", "dot_xy", "dot_xx", "chain"]
+
+
+def flag_sets():
+    for bits in range(1 << len(FLAGS)):
+        f = {n for k, n in enumerate(FLAGS) if bits >> k & 1}
+        if "shift" in f and "vshift" in f:
+            continue
+        yield f
+
+
+ALL = {"scale", "vshift", "axpby", "dot_yy", "dot_xy", "dot_xx", "chain"}
+
+
+@pytest.fixture(scope="module")
+def irregular():
+    return gen.irregular_band(3001, lmin=0, lmax=40, band=200, seed=12)
+
+
+@pytest.mark.parametrize("w", [1, 3, 16])
+def test_all_flag_subsets(cuda_ok, irregular, w):
+    mat = sellcs.SellMatrix(irregular, C=32, sigma=256)
+    for f in flag_sets():
+        run_case(irregular, 32, 256, w, f, mat=mat, seed=len(f))
+
+
+@pytest.mark.parametrize("C,sigma", list(itertools.product([8, 16, 32], [1, 32, 256, 1024])))
+def test_chunk_and_window_grid(cuda_ok, irregular, C, sigma):
+    mat = sellcs.SellMatrix(irregular, C=C, sigma=sigma)
+    for w in (1, 2, 3, 4, 7, 8, 16, 33):
+        run_case(irregular, C, sigma, w, ALL, mat=mat, seed=w)
+    run_case(irregular, C, sigma, 1, set(), mat=mat)
+
+
+@pytest.mark.parametrize("vdt,xdt", [("f64", "f64"), ("f32", "f64"), ("bf16", "f64"), ("f32", "f32"),
+                                     ("bf16", "f32")])
+@pytest.mark.parametrize("w", [1, 2, 4, 5, 8, 16, 32])
+def test_precisions(cuda_ok, irregular, vdt, xdt, w):
+    run_case(irregular, 32, 256, w, ALL, vdt=vdt, xdt=xdt, seed=w)
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 6, 16])
+@pytest.mark.parametrize("layout,pad", [("row", 3), ("col", 0), ("col", 5)])
+def test_layouts_and_leading_dimension(cuda_ok, irregular, w, layout, pad):
+    run_case(irregular, 32, 32, w, ALL, layout=layout, ld_pad=pad, seed=w)
+
+
+def test_rectangular(cuda_ok):
+    rng = np.random.default_rng(4)
+    A = random_csr(300, 517, 0.05, rng)
+    for w in (1, 4, 9):
+        run_case(A, 16, 64, w, {"scale", "axpby", "chain", "dot_yy"}, seed=w)
+    with pytest.raises(sellcs.SpError) as e:
+        run_case(A, 16, 64, 2, {"dot_xy"})
+    assert e.value.code == sellcs.SP_ERR_DIM
+
+
+@pytest.mark.parametrize("N", [1, 5, 31, 33, 64])
+def test_small_shapes(cuda_ok, N):
+    rng = np.random.default_rng(N)
+    A = random_csr(N, N, 0.4, rng)
+    for C, sigma in [(1, 1), (4, 3), (32, 1), (32, 1000), (64, 64)]:
+        run_case(A, C, sigma, 1, ALL, seed=C)
+        run_case(A, C, sigma, 5, ALL, seed=C + 1)
+
+
+def test_empty_rows_and_long_row(cuda_ok):
+    N = 2000
+    rng = np.random.default_rng(8)
+    lens = rng.integers(0, 4, N)
+    lens[rng.integers(N)] = N  # one dense row
+    lens[::7] = 0
+    rowptr = np.zeros(N + 1, np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    col = np.concatenate([np.sort(rng.choice(N, size=l, replace=False)) for l in lens]).astype(np.int32)
+    A = gen.CSR(N, N, rowptr, col, rng.uniform(-1, 1, rowptr[-1]))
+    for sigma in (1, 128, N):
+        run_case(A, 32, sigma, 1, ALL)
+        run_case(A, 32, sigma, 8, ALL)
+
+
+def test_empty_matrix(cuda_ok):
+    A = gen.CSR(0, 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    mat = sellcs.SellMatrix(A, C=32, sigma=1)
+    assert mat.info()["nchunks"] == 0
+    x = torch.zeros(0, 2, dtype=torch.float64, device="cuda")
+    y = torch.zeros(0, 2, dtype=torch.float64, device="cuda")
+    dot = torch.full((6,), 7.0, dtype=torch.float64, device="cuda")
+    sellcs.spmv(mat, x, y, dot_yy=True, dot_xx=True, dot=dot)
+    d = dot.cpu().numpy()
+    assert d[0] == 0 and d[1] == 0 and d[4] == 0 and d[5] == 0 and d[2] == 7.0
+
+
+def test_all_zero_pattern(cuda_ok):
+    N = 100
+    A = gen.CSR(N, N, np.zeros(N + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    run_case(A, 32, 1, 3, ALL)
+
+
+def test_beta_off_ignores_nan_y_and_deterministic_dots(cuda_ok):
+    A = gen.irregular_band(20000, band=500, seed=3)
+    mat = sellcs.SellMatrix(A, C=32, sigma=256)
+    x = to_dev(gen.block_vector(A.nrows, 4, 1))
+    outs = []
+    for _ in range(3):
+        y = torch.full((A.nrows, 4), float("nan"), dtype=torch.float64, device="cuda")
+        d = sellcs.spmv(mat, x, y, dot_yy=True, dot_xy=True)
+        torch.cuda.synchronize()
+        assert torch.isfinite(y).all()
+        outs.append(d.cpu().numpy().copy())
+    np.testing.assert_array_equal(outs[0][:8], outs[1][:8])
+    np.testing.assert_array_equal(outs[0][:8], outs[2][:8])
+
+
+def test_aliasing_and_argument_errors(cuda_ok, irregular):
+    mat = sellcs.SellMatrix(irregular, C=32, sigma=1)
+    x = to_dev(np.ones((irregular.nrows, 2)))
+    with pytest.raises(sellcs.SpError) as e:
+        sellcs.spmv(mat, x, x)
+    assert e.value.code == sellcs.SP_ERR_ARG
+    y = torch.zeros_like(x)
+    with pytest.raises(sellcs.SpError) as e:
+        sellcs.spmv(mat, x, y, z=x, delta=1.0, eta=1.0)
+    assert e.value.code == sellcs.SP_ERR_ARG
+    with pytest.raises(sellcs.SpError) as e:
+        sellcs.spmv(mat, x[:-1], y)
+    assert e.value.code == sellcs.SP_ERR_DIM
+    with pytest.raises(sellcs.SpError) as e:
+        sellcs.spmv(mat, x.float(), y.float())  # f64 values need f64 vectors
+    assert e.value.code == sellcs.SP_ERR_DTYPE
+
+
+def test_dot_to_host_pointer(cuda_ok, irregular):
+    import ctypes as ct
+    mat = sellcs.SellMatrix(irregular, C=32, sigma=32)
+    X = gen.block_vector(irregular.nrows, 3, 9)
+    x = to_dev(X)
+    y = torch.zeros_like(x)
+    hx, hy = sellcs.sp_dense_view(x), sellcs.sp_dense_view(y)
+    host = np.full(9, np.nan)
+    o, keep = sellcs.make_opts(3, dot_xx=True, dot_yy=True, dot_ptr=host.ctypes.data_as(ct.c_void_p),
+                               dot_host=True)
+    sellcs.check(sellcs.lib().sp_spmv(hy, mat.handle, hx, ct.byref(o), sellcs._stream(None)), "spmv")
+    yr, dr, _ = oracle.spmmv(irregular, X, dot_yy=True, dot_xx=True)
+    np.testing.assert_allclose(host[6:], dr[6:], rtol=1e-13)
+    np.testing.assert_allclose(host[:3], dr[:3], rtol=1e-12)
+    assert np.all(np.isnan(host[3:6]))
+    sellcs.sp_dense_destroy(hx)
+    sellcs.sp_dense_destroy(hy)
