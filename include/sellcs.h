@@ -225,6 +225,79 @@ SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spm
 SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
                     void *stream);
 
+/* ------------------------------------------------------------------ batched SpMMV */
+
+/*
+ * Many matrices of uneven size and block width in ONE persistent launch (no
+ * counterpart in the paper beyond its block vectors; Sec. "Block vectors").
+ * Each matrix's rows are cut into cost-balanced units that the resident warps
+ * own statically, so the per-matrix dot products are deterministic.
+ *   A[m]            matrices (all with the same value precision; not owned,
+ *                   must outlive the batch)
+ *   widths[m]       block width of matrix m, 1..SP_BATCH_MAX_W
+ *   cols_per_lane   per matrix, the columns each lane owns (1,2,4,8; must
+ *                   divide widths[m]); NULL or 0 entries: chosen automatically
+ *   vec_dtype       SP_F64 (f64 values) or SP_F32 (f32 values: f32 or f64 vectors)
+ * Synchronises the stream.
+ */
+#define SP_BATCH_MAX_W 8
+typedef struct sp_batch sp_batch;
+SP_API int sp_batch_create(sp_batch **out, int count, sp_mat *const *A, const int32_t *widths,
+                           const int32_t *cols_per_lane, sp_dtype vec_dtype, void *stream);
+/* Bind the block vectors: x[m] (ncols x w, row-major, ld = w), y[m] (nrows x w),
+ * y0[m] the beta source (NULL or NULL entries: y itself).  Device pointers,
+ * 16-byte aligned.  Synchronises the stream. */
+SP_API int sp_batch_bind(sp_batch *b, const void *const *x, void *const *y, const void *const *y0,
+                         void *stream);
+/* y_m = alpha A_m x_m + beta y0_m for every m in one launch.  flags: any of
+ * SP_SPMV_SCALE, SP_SPMV_AXPBY, SP_SPMV_DOT_YY/XY/XX; dots (device) receives
+ * for matrix m at dots[m*3*SP_BATCH_MAX_W + q*SP_BATCH_MAX_W + k] the sums
+ * q = 0: <y,y>, 1: <x,y>, 2: <x,x> of column k (a second small launch).
+ * Asynchronous; graph-capturable once bound. */
+SP_API int sp_batch_spmv(sp_batch *b, uint32_t flags, double alpha, double beta, double *dots, void *stream);
+/* Units, grid and the lane layout chosen per matrix (host outputs, any may be NULL). */
+SP_API int sp_batch_info(const sp_batch *b, int32_t *nunits, int32_t *grid, int32_t *cols_per_lane);
+SP_API int sp_batch_destroy(sp_batch *b, void *stream);
+
+/* ------------------------------------------------------------------ mixed-precision CG */
+
+/*
+ * Batched CG with iterative refinement for SPD matrices: per column the
+ * float64 residual r = b - A x (batched float64 product), a float32 CG solve
+ * of A d = r / ||r|| to relative reduction inner_tol (Chronopoulos-Gear form:
+ * one batched product with fused <r,r>, <r,Ar> and one vector update per
+ * iteration, graph_iters iterations per CUDA-graph replay), and the float64
+ * update x += ||r|| d, until ||b - A x||_2 <= tol ||b||_2 for every column.
+ * inner_f64 = 1 runs the inner solve in float64 (plain CG reference).
+ */
+typedef struct {
+    double tol;
+    double inner_tol;
+    int32_t max_outer;
+    int32_t max_inner;
+    int32_t graph_iters;
+    int32_t inner_f64;
+} sp_cg_opts;
+#define SP_CG_OPTS_INIT {1e-10, 1e-4, 40, 20000, 16, 0}
+typedef struct {
+    int32_t outer;          /* refinement steps taken */
+    int32_t inner;          /* inner iterations summed over refinement steps (slowest column) */
+    int32_t graph_launches; /* CUDA graph replays */
+    int32_t converged;      /* 1 if every column met tol */
+    double max_rel_residual;
+} sp_cg_stats;
+typedef struct sp_cg sp_cg;
+/* A[m]: float64 square SPD matrices (not owned; a float32 copy is made),
+ * widths[m] in 1..SP_BATCH_MAX_W, cpl64/cpl32: lane layouts (NULL = auto). */
+SP_API int sp_cg_create(sp_cg **out, int count, sp_mat *const *A, const int32_t *widths, const int32_t *cpl64,
+                        const int32_t *cpl32, void *stream);
+/* b[m], x[m]: device float64 row-major n_m x w_m.  rel_res (host, sum of
+ * widths, may be NULL) receives the final relative residual of each column.
+ * Synchronous. */
+SP_API int sp_cg_solve(sp_cg *cg, const double *const *b, double *const *x, const sp_cg_opts *opts,
+                       sp_cg_stats *stats, double *rel_res, void *stream);
+SP_API int sp_cg_destroy(sp_cg *cg, void *stream);
+
 /* ------------------------------------------------------------------ device info */
 /* Streaming multiprocessor count of the current device (for grid sizing tests). */
 SP_API int sp_device_sm_count(int *count);

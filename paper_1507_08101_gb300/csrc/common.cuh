@@ -55,6 +55,13 @@ struct Pattern {
     DevBufPtr rowptr;    // int64[nrows+1], the CSR row pointers (original order)
     // for the transpose only: position in the parent's CSR of each of its own CSR entries
     DevBufPtr src_index; // int64[nnz]
+    // Static work partition of the persistent kernels: for a grid of
+    // SMs * b blocks (b = 1..kMaxOcc) of kPartWarps warps, warp t owns the
+    // 32-slot blocks [bounds[off[b] + t], bounds[off[b] + t + 1]), chosen so
+    // that every warp gets the same share of (stored entries + 2 per row).
+    DevBufPtr bounds;    // int32
+    int64_t bounds_off[9] = {0};
+    int32_t bounds_sms = 0;
 };
 using PatternPtr = std::shared_ptr<Pattern>;
 
@@ -131,5 +138,16 @@ int launch_sampled(const Pattern &P, sp_dtype xdt, int w, const void *x, const v
                    cudaStream_t s);
 
 int device_sm_count(int *n);
+int build_partition(Pattern &P, cudaStream_t s);
+constexpr int kPartWarps = 8;  // warps per block of the partitioned kernels
+constexpr int kMaxOcc = 8;     // resident blocks per SM covered by the partition table
+// Partition table for a grid of `grid` blocks, or null when the grid is not
+// SMs * b for b <= kMaxOcc (then the kernels fall back to a block-strided loop).
+inline const int32_t *partition_for(const Pattern &P, int64_t grid) {
+    if (!P.bounds || P.bounds_sms <= 0 || grid % P.bounds_sms) return nullptr;
+    int64_t b = grid / P.bounds_sms;
+    if (b < 1 || b > kMaxOcc) return nullptr;
+    return (const int32_t *)P.bounds->ptr + P.bounds_off[b];
+}
 
 }  // namespace sp

@@ -358,6 +358,76 @@ int fill_values_from_csr(const Pattern &P, sp_dtype vdt, void *val_sell, const v
     return SP_OK;
 }
 
+// ------------------------------------------------------------------ static work partition
+
+// cost of each 32-slot block: stored-entry work of its rows + 2 per real row
+// (the epilogue); slots >= nrows are padding rows
+__global__ void k_block32_cost(const int32_t *__restrict__ slotlen, int64_t nslots, int64_t nrows,
+                               int64_t nb32, int64_t *__restrict__ cost) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb32;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        int64_t e = min(32 * k + 32, nslots);
+        for (int64_t s = 32 * k; s < e; ++s) c += slotlen[s] + (s < nrows ? 2 : 0);
+        cost[k] = c;
+    }
+}
+
+// bounds[t] = first block whose prefix cost reaches t/T of the total
+__global__ void k_partition(const int64_t *__restrict__ prefix, int64_t nb32, int64_t T,
+                            int32_t *__restrict__ bounds) {
+    int64_t total = prefix[nb32];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k;
+        if (t == 0) {
+            k = 0;
+        } else if (t == T) {
+            k = nb32;
+        } else {
+            int64_t target = (total * t + T / 2) / T;
+            int64_t lo = 0, hi = nb32;
+            while (lo < hi) {
+                int64_t m = (lo + hi) >> 1;
+                if (prefix[m] < target) lo = m + 1; else hi = m;
+            }
+            k = lo;
+        }
+        bounds[t] = (int32_t)k;
+    }
+}
+
+int build_partition(Pattern &P, cudaStream_t s) {
+    int sms = 1;
+    SP_TRY(device_sm_count(&sms));
+    int64_t nb32 = (P.nslots + 31) / 32;
+    if (nb32 >= (1LL << 31)) return SP_OK;
+    Tmp cost(s), prefix(s);
+    SP_TRY(cost.alloc((nb32 + 1) * sizeof(int64_t)));
+    SP_TRY(prefix.alloc((nb32 + 1) * sizeof(int64_t)));
+    SP_CUDA(cudaMemsetAsync(cost.p, 0, (nb32 + 1) * sizeof(int64_t), s));
+    if (nb32 > 0) {
+        k_block32_cost<<<grid_for(nb32), kThreads, 0, s>>>((const int32_t *)P.slotlen->ptr, P.nslots, P.nrows,
+                                                            nb32, cost.as<int64_t>());
+        SP_CUDA(cudaGetLastError());
+    }
+    SP_TRY(scan_exclusive(cost.as<int64_t>(), prefix.as<int64_t>(), nb32 + 1, s));
+    int64_t total = 0;
+    for (int b = 1; b <= kMaxOcc; ++b) {
+        P.bounds_off[b] = total;
+        total += (int64_t)kPartWarps * b * sms + 1;
+    }
+    SP_TRY(dev_alloc(P.bounds, total * sizeof(int32_t), s));
+    for (int b = 1; b <= kMaxOcc; ++b) {
+        int64_t T = (int64_t)kPartWarps * b * sms;
+        k_partition<<<grid_for(T + 1), kThreads, 0, s>>>(prefix.as<int64_t>(), nb32, T,
+                                                          (int32_t *)P.bounds->ptr + P.bounds_off[b]);
+        SP_CUDA(cudaGetLastError());
+    }
+    P.bounds_sms = sms;
+    return SP_OK;
+}
+
 // ------------------------------------------------------------------ whole construction
 
 int build_pattern_and_values(sp_mat *A, int64_t N, int64_t ncols, const int64_t *d_rowptr,
@@ -449,6 +519,7 @@ int build_pattern_and_values(sp_mat *A, int64_t N, int64_t ncols, const int64_t 
             (const int64_t *)P->chunkptr->ptr, P->nslots, C, (int32_t *)P->col->ptr);
         SP_CUDA(cudaGetLastError());
     }
+    SP_TRY(build_partition(*P, s));
     DevBufPtr val;
     SP_TRY(dev_alloc(val, nstored * dtype_size(A->vdt), s));
     SP_TRY(fill_values_from_csr(*P, A->vdt, val->ptr, d_val, val_f32, s));

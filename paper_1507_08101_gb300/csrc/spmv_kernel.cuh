@@ -61,24 +61,47 @@ struct SpmvArgs {
     int32_t dot_stride, dot_off;
     double *partials;
     unsigned *ticket;
+    const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
+    const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
     double gamma[kMaxTileW];
 };
+
+// Tuning knobs (compile-time): unroll depth of the row loop for narrow lanes,
+// and the minimum resident blocks per SM requested for the width-1 variants.
+#ifndef SP_UNROLL_NARROW
+#define SP_UNROLL_NARROW 8
+#endif
+#ifndef SP_UNROLL_WIDE
+#define SP_UNROLL_WIDE 2
+#endif
+#ifndef SP_MINB_W1
+#define SP_MINB_W1 1
+#endif
 
 template <class VT, class XT>
 struct AccOf { using T = float; };
 template <>
 struct AccOf<double, double> { using T = double; };
 
+// Widest run of columns one lane owns (compile-time knob per vector precision).
+#ifndef SP_CPL_MAX_F64
+#define SP_CPL_MAX_F64 4
+#endif
+#ifndef SP_CPL_MAX_F32
+#define SP_CPL_MAX_F32 8
+#endif
+
 template <class XT, int WP>
 __host__ __device__ constexpr int cols_per_lane() {
-    return (int)(16 / sizeof(XT)) * 2 < WP ? (int)(16 / sizeof(XT)) * 2 : WP;
+    return (sizeof(XT) == 8 ? SP_CPL_MAX_F64 : SP_CPL_MAX_F32) < WP ? (sizeof(XT) == 8 ? SP_CPL_MAX_F64 : SP_CPL_MAX_F32)
+                                                                      : WP;
 }
 
 // Host mirror of cols_per_lane for a runtime width.
 inline int host_cols_per_lane(size_t xsize, int w) {
     int wp = 1;
     while (wp < w) wp <<= 1;
-    int c = (int)(16 / xsize) * 2;
+    int c = xsize == 8 ? SP_CPL_MAX_F64 : SP_CPL_MAX_F32;
     return c < wp ? c : wp;
 }
 
@@ -91,6 +114,16 @@ __device__ __forceinline__ float val_to_acc<float, __nv_bfloat16>(__nv_bfloat16 
 
 template <class T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+// Epilogue arithmetic with every product and sum rounded on its own (no
+// contraction into fused multiply-adds), so that each kernel that applies the
+// same epilogue to the same row sum gets the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
 // Load CPL consecutive columns of one row of a block vector.
 // VEC: all CPL columns valid, unit column stride, address aligned to
@@ -264,13 +297,14 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 }
 
 template <class VT, class XT, int WP, bool VEC>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ SpmvArgs a) {
+__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
+    k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
     constexpr int ROWS = R * kSpmvWarps;
-    constexpr int U = CPL >= 4 ? 2 : 4;
+    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % G, rw = lane / G;
@@ -294,11 +328,11 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ 
     for (int c = 0; c < CPL; ++c) dyy[c] = dxy[c] = dxx[c] = 0.0;
 
     const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
-    for (int64_t base = (int64_t)blockIdx.x * ROWS; base < a.nslots; base += (int64_t)gridDim.x * ROWS) {
-        const int64_t s = base + warp * R + rw;
-        if (s >= a.nslots) continue;
+
+    // one row slot: row sums, then y = alpha (t - gamma x_i) + beta y_i, dots, chain
+    auto slot = [&](int64_t s) {
         const int64_t i = a.perm ? (int64_t)a.perm[s] : (s < a.nrows ? s : -1);
-        if (i < 0) continue;
+        if (i < 0) return;
         const uint32_t cidx = (uint32_t)s / (uint32_t)a.C;
         const int r = (int)((uint32_t)s - cidx * (uint32_t)a.C);
         const int64_t off = a.chunkptr[cidx] + r;
@@ -307,9 +341,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ 
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
         row_product<VT, XT, AT, CPL, VEC, U>(val + off, a.col + off, a.C, len, xk, a.xrs, a.xcs, nvalid, acc);
-        if (nvalid <= 0) continue;
-
-        // epilogue: y = alpha (t - gamma x_i) + beta y_i, dots, chain
+        if (nvalid <= 0) return;
         XT xi[CPL], yo[CPL], t[CPL];
         if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
         XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
@@ -317,9 +349,9 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ 
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             XT v = (XT)acc[c];
-            if (shift) v = v - gam[c] * xi[c];
-            if (f & SP_SPMV_SCALE) v = alpha * v;
-            if (f & SP_SPMV_AXPBY) v = v + beta * yo[c];
+            if (shift) v = sub_rn(v, mul_rn(gam[c], xi[c]));
+            if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
+            if (f & SP_SPMV_AXPBY) v = add_rn(v, mul_rn(beta, yo[c]));
             t[c] = v;
         }
         store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
@@ -339,8 +371,22 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmmv(const __grid_constant__ 
             XT *zp = z + i * a.zrs + (int64_t)k0 * a.zcs;
             load_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) zo[c] = delta * zo[c] + eta * t[c];
+            for (int c = 0; c < CPL; ++c) zo[c] = add_rn(mul_rn(delta, zo[c]), mul_rn(eta, t[c]));
             store_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
+        }
+    };
+
+    if (a.wbounds) {
+        // static cost-balanced partition: this warp owns a contiguous slot range
+        const int gw = blockIdx.x * kSpmvWarps + warp;
+        const int64_t s0 = (int64_t)a.wbounds[gw] * 32;
+        const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
+        const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
+        for (int64_t s = s0 + rw; s < s1; s += R) slot(s);
+    } else {
+        for (int64_t base = (int64_t)blockIdx.x * ROWS; base < a.nslots; base += (int64_t)gridDim.x * ROWS) {
+            const int64_t s = base + warp * R + rw;
+            if (s < a.nslots) slot(s);
         }
     }
     if (dots) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);

@@ -32,7 +32,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     if (grid > max_blocks) grid = max_blocks;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_spmmv<VT, XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(a);
+    SpmvArgs b = a;
+    b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid) : nullptr;
+    k_spmmv<VT, XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -49,6 +49,19 @@ class sp_spmv_opts(ct.Structure):
                 ("dot", ct.c_void_p)]
 
 
+class sp_cg_opts_t(ct.Structure):
+    _fields_ = [("tol", ct.c_double), ("inner_tol", ct.c_double), ("max_outer", ct.c_int32),
+                ("max_inner", ct.c_int32), ("graph_iters", ct.c_int32), ("inner_f64", ct.c_int32)]
+
+
+class sp_cg_stats_t(ct.Structure):
+    _fields_ = [("outer", ct.c_int32), ("inner", ct.c_int32), ("graph_launches", ct.c_int32),
+                ("converged", ct.c_int32), ("max_rel_residual", ct.c_double)]
+
+
+SP_BATCH_MAX_W = 8
+
+
 class SpError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -82,6 +95,14 @@ _SIGS = {
     "sp_dense_destroy": (I, [P, P]),
     "sp_spmv": (I, [P, P, P, ct.POINTER(sp_spmv_opts), P]),
     "sp_spmv_adjoint": (I, [P, P, P, P, P, P]),
+    "sp_batch_create": (I, [PP, I, P, P, P, I, P]),
+    "sp_batch_bind": (I, [P, P, P, P, P]),
+    "sp_batch_spmv": (I, [P, ct.c_uint32, ct.c_double, ct.c_double, P, P]),
+    "sp_batch_info": (I, [P, P, P, P]),
+    "sp_batch_destroy": (I, [P, P]),
+    "sp_cg_create": (I, [PP, I, P, P, P, P, P]),
+    "sp_cg_solve": (I, [P, P, P, ct.POINTER(sp_cg_opts_t), ct.POINTER(sp_cg_stats_t), P, P]),
+    "sp_cg_destroy": (I, [P, P]),
 }
 
 
@@ -390,3 +411,92 @@ def spmv_adjoint(A: SellMatrix, g, x=None, dx=None, dvals=None, stream=None):
         for h in (hg, hx, hdx):
             if h is not None:
                 L.sp_dense_destroy(h, None)
+
+
+# ------------------------------------------------------------------ batches
+
+
+def _ptr_array(ptrs):
+    arr = (ct.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p if isinstance(p, int) else (p.value if isinstance(p, ct.c_void_p) else p.data_ptr())
+    return arr
+
+
+class Batch:
+    """Many SELL matrices multiplied in one persistent launch (sp_batch_*)."""
+
+    def __init__(self, mats, widths, cols_per_lane=None, vec_dtype="f64", stream=None):
+        self._lib = lib()
+        self.mats = list(mats)  # keep alive
+        self.count = len(self.mats)
+        self.widths = np.ascontiguousarray(widths, np.int32)
+        cpl = None if cols_per_lane is None else np.ascontiguousarray(cols_per_lane, np.int32)
+        h = ct.c_void_p()
+        check(self._lib.sp_batch_create(ct.byref(h), self.count, _ptr_array([m.handle.value for m in self.mats]),
+                                        _ptr(self.widths), _ptr(cpl), DTYPES[vec_dtype], _stream(stream)),
+              "sp_batch_create")
+        self.handle = h
+
+    def bind(self, xs, ys, y0s=None, stream=None):
+        self._bound = (list(xs), list(ys), None if y0s is None else list(y0s))
+        y0 = None if y0s is None else _ptr_array(y0s)
+        check(self._lib.sp_batch_bind(self.handle, _ptr_array(xs), _ptr_array(ys), y0, _stream(stream)),
+              "sp_batch_bind")
+
+    def spmv(self, flags=0, alpha=1.0, beta=0.0, dots=None, stream=None):
+        check(self._lib.sp_batch_spmv(self.handle, flags, alpha, beta, _ptr(dots), _stream(stream)),
+              "sp_batch_spmv")
+
+    def info(self):
+        nu, gr = ct.c_int32(), ct.c_int32()
+        cpl = np.zeros(self.count, np.int32)
+        check(self._lib.sp_batch_info(self.handle, ct.byref(nu), ct.byref(gr), _ptr(cpl)), "sp_batch_info")
+        return {"nunits": nu.value, "grid": gr.value, "cols_per_lane": cpl}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sp_batch_destroy(self.handle, _stream(None))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CG:
+    """Batched mixed-precision CG with iterative refinement (sp_cg_*)."""
+
+    def __init__(self, mats, widths, cpl64=None, cpl32=None, stream=None):
+        self._lib = lib()
+        self.mats = list(mats)
+        self.count = len(self.mats)
+        self.widths = np.ascontiguousarray(widths, np.int32)
+        c64 = None if cpl64 is None else np.ascontiguousarray(cpl64, np.int32)
+        c32 = None if cpl32 is None else np.ascontiguousarray(cpl32, np.int32)
+        h = ct.c_void_p()
+        check(self._lib.sp_cg_create(ct.byref(h), self.count, _ptr_array([m.handle.value for m in self.mats]),
+                                     _ptr(self.widths), _ptr(c64), _ptr(c32), _stream(stream)), "sp_cg_create")
+        self.handle = h
+
+    def solve(self, bs, xs, tol=1e-10, inner_tol=1e-4, max_outer=40, max_inner=20000, graph_iters=16,
+              inner_f64=False, stream=None):
+        o = sp_cg_opts_t(tol, inner_tol, max_outer, max_inner, graph_iters, int(inner_f64))
+        st = sp_cg_stats_t()
+        rel = np.zeros(int(self.widths.sum()))
+        check(self._lib.sp_cg_solve(self.handle, _ptr_array(bs), _ptr_array(xs), ct.byref(o), ct.byref(st),
+                                    _ptr(rel), _stream(stream)), "sp_cg_solve")
+        return {f: getattr(st, f) for f, _ in sp_cg_stats_t._fields_}, rel
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sp_cg_destroy(self.handle, _stream(None))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
