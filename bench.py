@@ -269,6 +269,244 @@ def run_ours(args, rank, world):
     return result, (A, X, Y0, Z0)
 
 
+# ------------------------------------------------------------------ secondary workloads
+
+
+def _events_time(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps  # ms
+
+
+def secondary_laplace(peak):
+    """Laplacian 32^3 (SELL-32-1, plain y = A x, f64): cold (L2 flushed before
+    each launch) and warm (CUDA graph of 1000 back-to-back launches), plus the
+    same stencil at 256^3 as the HBM-bound companion."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    from workloads import generators as gen
+    out = {}
+    for n in (32, 256):
+        A = gen.laplace3d(n)
+        m = sellcs.SellMatrix(A, C=32, sigma=1)
+        inf = m.info()
+        x = torch.from_numpy(gen.block_vector(A.nrows, 1, gen.BASE_SEED + 1)[:, 0]).cuda()
+        y = torch.zeros_like(x)
+        nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * 32, 1, 8, 8, False, False,
+                               False)
+        stream = torch.cuda.Stream()
+        hx, hy = sellcs.sp_dense_view(x), sellcs.sp_dense_view(y)
+        import ctypes as ct
+        o, _ = sellcs.make_opts(1)
+        L = sellcs.lib()
+        sp = ct.c_void_p(stream.cuda_stream)
+
+        def call():
+            L.sp_spmv(hy, m.handle, hx, ct.byref(o), sp)
+
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                call()
+            torch.cuda.synchronize()
+            flush = torch.empty(2 * 129 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            cold = []
+            for _ in range(20):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                cold.append(e0.elapsed_time(e1))
+            del flush
+            cold_ms = statistics.median(cold)
+            g = torch.cuda.CUDAGraph()
+            R = 1000 if n == 32 else 20
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(R):
+                    call()
+            g.replay()
+            torch.cuda.synchronize()
+            warm_ms = _events_time(g.replay, 5, stream) / R
+        sellcs.sp_dense_destroy(hx)
+        sellcs.sp_dense_destroy(hy)
+        out[f"laplace{n}"] = {"nnz": A.nnz, "bytes_per_call": nb,
+                              "cold_us": round(cold_ms * 1e3, 2), "cold_GBs": round(nb / cold_ms / 1e6, 1),
+                              "warm_graph_us": round(warm_ms * 1e3, 3), "warm_graph_GBs": round(nb / warm_ms / 1e6, 1),
+                              "warm_frac_of_peak": round(nb / warm_ms / 1e6 / peak, 4)}
+        del m, x, y
+    out["laplace32"]["note"] = ("3.2 MB working set: the warm number is served from L2 and is not an HBM figure; "
+                                "the cold number is dominated by launch and ramp latency")
+    return out
+
+
+def _row_sample_csr(A, rows):
+    from workloads.generators import CSR
+    lens = A.rowptr[rows + 1] - A.rowptr[rows]
+    rp = np.zeros(rows.size + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows])
+    return CSR(rows.size, A.ncols, rp, A.col[idx], A.val[idx])
+
+
+def secondary_anderson(peak):
+    """Anderson 128^3, width-16 Chebyshev step (alpha = 2/a, beta = -1) in each
+    precision pair: GB/s, speedup over f64, max error on 2048 sampled rows
+    against the f64 oracle (relative to max |y|)."""
+    import ctypes as ct
+    import torch
+    import oracle
+    from paper_1507_08101_gb300 import sellcs
+    from workloads import generators as gen
+    A, X = gen.workload_anderson()
+    a = 1.01 * (6 + 8.25)
+    rows = np.sort(np.random.default_rng(0).choice(A.nrows, 2048, replace=False))
+    sub = _row_sample_csr(A, rows)
+    Y0 = gen.block_vector(A.nrows, 16, gen.BASE_SEED + 2, tag=77)
+    yref = oracle.spmmv(sub, X, alpha=2 / a, beta=-1.0, y0=Y0[rows])[0]
+    out = {}
+    base = None
+    for vdt, xdt in [("f64", "f64"), ("f32", "f64"), ("bf16", "f64"), ("f32", "f32"), ("bf16", "f32")]:
+        m = sellcs.SellMatrix(A, C=32, sigma=1, dtype=vdt)
+        inf = m.info()
+        tdt = torch.float64 if xdt == "f64" else torch.float32
+        x = torch.from_numpy(X).to("cuda", tdt)
+        y0 = torch.from_numpy(Y0).to("cuda", tdt)
+        y = y0.clone()
+        hx, hy = sellcs.sp_dense_view(x), sellcs.sp_dense_view(y)
+        o, _ = sellcs.make_opts(16, alpha=2 / a, beta=-1.0)
+        L = sellcs.lib()
+        stream = torch.cuda.current_stream()
+        sp = ct.c_void_p(stream.cuda_stream)
+        L.sp_spmv(hy, m.handle, hx, ct.byref(o), sp)
+        torch.cuda.synchronize()
+        err = float(np.abs(y.double().cpu().numpy()[rows] - yref).max() / np.abs(yref).max())
+        for _ in range(3):
+            L.sp_spmv(hy, m.handle, hx, ct.byref(o), sp)
+        ms = _events_time(lambda: L.sp_spmv(hy, m.handle, hx, ct.byref(o), sp), 30, stream)
+        sv = {"f64": 8, "f32": 4, "bf16": 2}[vdt]
+        sx = 8 if xdt == "f64" else 4
+        nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * 32, 16, sv, sx, True,
+                               False, False)
+        if base is None:
+            base = ms
+        out[f"{vdt}_vals_{xdt}_vecs"] = {"us": round(ms * 1e3, 1), "GBs": round(nb / ms / 1e6, 1),
+                                         "frac_of_peak": round(nb / ms / 1e6 / peak, 4),
+                                         "speedup_vs_f64": round(base / ms, 3), "max_rel_err_vs_f64_oracle": err,
+                                         "bytes_per_call": nb}
+        sellcs.sp_dense_destroy(hx)
+        sellcs.sp_dense_destroy(hy)
+        del m, x, y, y0
+    return out
+
+
+def secondary_powerlaw(peak):
+    """Power-law N = 2^20, f32, width 4: forward product and backward
+    (A^T g through the transposed matrix + sampled dvals)."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    from workloads import generators as gen
+    A, X, G = gen.workload_powerlaw()
+    m = sellcs.SellMatrix(A, C=32, sigma=256, dtype="f32", with_transpose=True)
+    inf = m.info()
+    x = torch.from_numpy(X).to("cuda", torch.float32)
+    g = torch.from_numpy(G).to("cuda", torch.float32)
+    y = torch.empty_like(x)
+    dx = torch.empty_like(x)
+    dv = torch.empty(A.nnz, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        sellcs.spmv(m, x, y)
+        sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv)
+    fwd = _events_time(lambda: sellcs.spmv(m, x, y), 50, stream)
+    bwd = _events_time(lambda: sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv), 50, stream)
+    nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * 32, 4, 4, 4, False, False, True)
+    # backward: A^T product (same byte count) + sampled: col index + dvals write per nonzero, g and x once
+    nb_bwd = nb + A.nnz * (4 + 4) + 2 * A.nrows * 4 * 4 + inf["nchunks"] * 32 * 8
+    return {"nnz": A.nnz, "fwd_us": round(fwd * 1e3, 1), "fwd_GBs": round(nb / fwd / 1e6, 1),
+            "bwd_us": round(bwd * 1e3, 1), "bwd_GBs": round(nb_bwd / bwd / 1e6, 1)}
+
+
+def secondary_cg_batch(peak):
+    """64 SPD systems L_2D(s) + 0.01 I, s in [64, 512], widths 1..8.
+    (a) one persistent batched f32 SpMMV launch vs one batched f64 launch vs 64
+    separate plain f64 sp_spmv launches; (b) mixed-precision CG time to
+    ||b - Ax|| <= 1e-10 ||b|| (f32 inner, graph-captured) vs the same driver
+    with a f64 inner solve.  C, sigma and lanes per row from the autotuner."""
+    import time as _t
+    import torch
+    from paper_1507_08101_gb300 import autotune, sellcs
+    from workloads import generators as gen
+    batch = gen.workload_cg_batch()
+    mats = [A for A, _ in batch]
+    Bs = [B for _, B in batch]
+    widths = [B.shape[1] for B in Bs]
+    t0 = _t.time()
+    cfg = autotune.tune_batch(mats, widths, dtype="f32", vec_dtype="f32",
+                              cache_path=os.path.join(ROOT, "_autotune_cache.json"))
+    tune_s = _t.time() - t0
+    S64 = [sellcs.SellMatrix(A, C=c["C"], sigma=c["sigma"], dtype="f64") for A, c in zip(mats, cfg)]
+    S32 = [s.clone("f32") for s in S64]
+    cpl32 = [c["cpl"] for c in cfg]
+    xs32 = [torch.rand(A.nrows, w, dtype=torch.float32, device="cuda") for A, w in zip(mats, widths)]
+    ys32 = [torch.empty_like(v) for v in xs32]
+    xs64 = [v.double() for v in xs32]
+    ys64 = [torch.empty_like(v) for v in xs64]
+    b32 = sellcs.Batch(S32, widths, cols_per_lane=cpl32, vec_dtype="f32")
+    b32.bind(xs32, ys32)
+    b64 = sellcs.Batch(S64, widths, vec_dtype="f64")
+    b64.bind(xs64, ys64)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        b32.spmv()
+        b64.spmv()
+    t32 = _events_time(b32.spmv, 50, stream)
+    t64 = _events_time(b64.spmv, 50, stream)
+
+    def separate():
+        for s, x, y in zip(S64, xs64, ys64):
+            sellcs.spmv(s, x, y)
+    separate()
+    tsep = _events_time(separate, 10, stream)
+    nnz = sum(A.nnz for A in mats)
+    rows = sum(A.nrows for A in mats)
+    nbw = sum(A.nrows * w for A, w in zip(mats, widths))
+    bytes32 = nnz * 8 + 2 * nbw * 4
+    bytes64 = nnz * 12 + 2 * nbw * 8
+    cg = sellcs.CG(S64, widths, cpl32=cpl32)
+    bs = [torch.from_numpy(B).cuda() for B in Bs]
+    xs = [torch.zeros_like(b) for b in bs]
+    cg.solve(bs, xs)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    t0 = _t.time()
+    st32, rel32 = cg.solve(bs, xs)
+    torch.cuda.synchronize()
+    tts32 = _t.time() - t0
+    cg.solve(bs, xs, inner_f64=True, inner_tol=1e-10, max_outer=3)
+    torch.cuda.synchronize()
+    t0 = _t.time()
+    st64, rel64 = cg.solve(bs, xs, inner_f64=True, inner_tol=1e-10, max_outer=3)
+    torch.cuda.synchronize()
+    tts64 = _t.time() - t0
+    return {"systems": len(mats), "rows": rows, "nnz": nnz, "rhs_columns": int(sum(widths)),
+            "autotune_s": round(tune_s, 2),
+            "tuned_configs": {f"C{C}_sigma{sg}_cpl{cp}": sum(1 for c in cfg if (c["C"], c["sigma"], c["cpl"]) == (C, sg, cp))
+                              for C, sg, cp in sorted({(c["C"], c["sigma"], c["cpl"]) for c in cfg})},
+            "spmv_batched_f32_us": round(t32 * 1e3, 1), "spmv_batched_f32_GBs": round(bytes32 / t32 / 1e6, 1),
+            "spmv_batched_f64_us": round(t64 * 1e3, 1), "spmv_batched_f64_GBs": round(bytes64 / t64 / 1e6, 1),
+            "spmv_64_separate_f64_us": round(tsep * 1e3, 1),
+            "speedup_batched_f32_vs_separate_f64": round(tsep / t32, 2),
+            "speedup_batched_f64_vs_separate_f64": round(tsep / t64, 2),
+            "mpcg_time_s": round(tts32, 4), "mpcg_stats": st32, "mpcg_max_rel_residual": float(rel32.max()),
+            "f64cg_time_s": round(tts64, 4), "f64cg_stats": st64, "f64cg_max_rel_residual": float(rel64.max()),
+            "speedup_mpcg_vs_f64cg": round(tts64 / tts32, 3)}
+
+
 # ------------------------------------------------------------------ CPU baseline (the oracle)
 
 
@@ -333,7 +571,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extra", action="store_true", help="also run the secondary workloads")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch"],
+                    help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -345,6 +585,13 @@ def main():
         return
 
     import torch
+    if args.only:
+        from paper_1507_08101_gb300 import build
+        build.build()
+        fns = {"laplace": secondary_laplace, "anderson_w16": secondary_anderson,
+               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch}
+        print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
+        return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
@@ -356,6 +603,17 @@ def main():
     result, data = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(data)
+    if rank == 0 and world == 1 and not args.no_secondary:
+        del data
+        peak = result["roofline"]["peak"]
+        sec = {}
+        for name, fn in (("laplace", secondary_laplace), ("anderson_w16", secondary_anderson),
+                         ("powerlaw_adjoint", secondary_powerlaw), ("cg_batch", secondary_cg_batch)):
+            try:
+                sec[name] = fn(peak)
+            except Exception as e:  # a failed secondary measurement must not hide the headline
+                sec[name] = {"error": f"{type(e).__name__}: {e}"}
+        result["secondary"] = sec
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -1,0 +1,113 @@
+"""Autotuner of the batched SpMMV launch configuration.
+
+For every matrix of a batch it picks the SELL chunk height C, the sort window
+sigma and the lane layout (columns per lane CPL, hence G = WP / CPL threads per
+row) by timing the candidates on the GPU: each candidate matrix is built with
+sp_mat_create_csr and multiplied through a one-matrix sp_batch (the same
+kernel the batch runs), timed with CUDA events.  Results are cached in a JSON
+file under a structural signature of the matrix (size, nonzeros, row-length
+histogram) and the block width, so equal structures are tuned once.
+
+This module only orchestrates calls into the CUDA library; the timed work is
+the library's kernels.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from . import sellcs
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sellcs_autotune.json")
+C_CANDIDATES = (8, 16, 32)
+SIGMA_CANDIDATES = (1, 32, 256, 1024)
+
+
+def signature(A, w: int, dtype: str) -> str:
+    lens = np.diff(np.asarray(A.rowptr))
+    h = hashlib.sha1()
+    h.update(np.bincount(lens).astype(np.int64).tobytes())
+    h.update(np.asarray(lens[: min(4096, lens.size)], np.int64).tobytes())
+    return f"{A.nrows}x{A.ncols}:{A.nnz}:w{w}:{dtype}:{h.hexdigest()[:16]}"
+
+
+def lane_candidates(w: int, xsize: int):
+    """Columns per lane that divide w and keep every row 8/16-byte aligned."""
+    wp = 1
+    while wp < w:
+        wp <<= 1
+    out = []
+    c = 1
+    while c <= min(wp, sellcs.SP_BATCH_MAX_W):
+        if w % c == 0 and (w * xsize) % min(16, c * xsize) == 0:
+            out.append(c)
+        c <<= 1
+    return out
+
+
+def _time_batch(batch, reps: int) -> float:
+    import torch
+    for _ in range(3):
+        batch.spmv()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        batch.spmv()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps  # microseconds
+
+
+def tune_matrix(A, w: int, dtype: str = "f32", vec_dtype: str = "f32", reps: int = 20,
+                Cs=C_CANDIDATES, sigmas=SIGMA_CANDIDATES) -> dict:
+    import torch
+    tdt = torch.float32 if vec_dtype == "f32" else torch.float64
+    xs = 4 if vec_dtype == "f32" else 8
+    x = torch.rand(A.ncols, w, dtype=tdt, device="cuda")
+    y = torch.empty(A.nrows, w, dtype=tdt, device="cuda")
+    best = None
+    for C in Cs:
+        for sigma in sigmas:
+            if sigma > 1 and sigma < C:
+                continue
+            m = sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=dtype)
+            for cpl in lane_candidates(w, xs):
+                b = sellcs.Batch([m], [w], cols_per_lane=[cpl], vec_dtype=vec_dtype)
+                b.bind([x], [y])
+                us = _time_batch(b, reps)
+                b.close()
+                if best is None or us < best["us"]:
+                    best = {"C": C, "sigma": sigma, "cpl": cpl, "us": round(us, 3)}
+            m.close()
+    return best
+
+
+def tune_batch(mats, widths, dtype: str = "f32", vec_dtype: str = "f32", cache_path: str | None = DEFAULT_CACHE,
+               reps: int = 20, Cs=C_CANDIDATES, sigmas=SIGMA_CANDIDATES):
+    """Per-matrix {C, sigma, cpl, us}; cached by structural signature."""
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    out = []
+    dirty = False
+    for A, w in zip(mats, widths):
+        key = signature(A, w, dtype)
+        if key not in cache:
+            cache[key] = tune_matrix(A, int(w), dtype, vec_dtype, reps, Cs, sigmas)
+            dirty = True
+        out.append(cache[key])
+    if cache_path and dirty:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=0, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return out

@@ -62,6 +62,7 @@ struct SpmvArgs {
     double *partials;
     unsigned *ticket;
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
+    int32_t nsm;             // SMs the grid was sized for
     const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
     double gamma[kMaxTileW];
 };
@@ -76,6 +77,9 @@ struct SpmvArgs {
 #endif
 #ifndef SP_MINB_W1
 #define SP_MINB_W1 1
+#endif
+#ifndef SP_MINB_WIDE
+#define SP_MINB_WIDE 1
 #endif
 
 template <class VT, class XT>
@@ -296,8 +300,16 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-template <class VT, class XT, int WP, bool VEC>
-__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
+// Swizzle of the block index before it picks its slice of the partition: with
+// SP_SWIZZLE blocks b, b + SMs, b + 2 SMs, ... (the blocks a one-wave launch
+// usually places on one SM) own consecutive slices, so each SM works on one
+// contiguous region and its L1 sees the x reuse of that region.
+#ifndef SP_SWIZZLE
+#define SP_SWIZZLE 0
+#endif
+
+template <class VT, class XT, int WP, bool VEC, bool DOTS>
+__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : SP_MINB_WIDE))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
@@ -311,7 +323,6 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
     const int k0 = gl * CPL;
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const uint32_t f = a.flags;
-    const bool dots = (f & SP_SPMV_DOT_ANY) != 0;
     const bool shift = (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0;
     const bool need_xi = shift || (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX));
     const VT *__restrict__ val = (const VT *)a.val;
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
             t[c] = v;
         }
         store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
-        if (dots) {
+        if constexpr (DOTS) {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 if (c < nvalid) {
@@ -378,7 +389,13 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
 
     if (a.wbounds) {
         // static cost-balanced partition: this warp owns a contiguous slot range
+#if SP_SWIZZLE
+        const int nsm = a.nsm, per = gridDim.x / nsm;
+        const int bsw = (blockIdx.x % nsm) * per + blockIdx.x / nsm;
+        const int gw = bsw * kSpmvWarps + warp;
+#else
         const int gw = blockIdx.x * kSpmvWarps + warp;
+#endif
         const int64_t s0 = (int64_t)a.wbounds[gw] * 32;
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
@@ -389,7 +406,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : 1))
             if (s < a.nslots) slot(s);
         }
     }
-    if (dots) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);
+    if constexpr (DOTS) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);
 }
 
 // Host-side dispatch over the block width for one (value, vector) type pair.

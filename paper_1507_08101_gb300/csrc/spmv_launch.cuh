@@ -11,14 +11,23 @@
 
 namespace sp {
 
-template <class VT, class XT, int WP, bool VEC>
+// Preferred shared-memory carveout (percent of the unified L1/shared array
+// given to shared memory); negative: leave the driver's choice.
+#ifndef SP_CARVEOUT
+#define SP_CARVEOUT -1
+#endif
+
+template <class VT, class XT, int WP, bool VEC, bool DOTS>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int ROWS = (32 / G) * kSpmvWarps;
     static int occ = 0;
     if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC>,
+        if (SP_CARVEOUT >= 0)
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 SP_CARVEOUT);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS>,
                                                                       kSpmvThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -34,15 +43,20 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     if (grid < 1) grid = 1;
     SpmvArgs b = a;
     b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid) : nullptr;
-    k_spmmv<VT, XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
+    b.nsm = sms;
+    k_spmmv<VT, XT, WP, VEC, DOTS><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
 template <class VT, class XT, int WP>
 static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
-    return vec ? launch_spmv_variant<VT, XT, WP, true>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false>(a, max_blocks, s);
+    const bool dots = (a.flags & SP_SPMV_DOT_ANY) != 0;
+    if (dots)
+        return vec ? launch_spmv_variant<VT, XT, WP, true, true>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, true>(a, max_blocks, s);
+    return vec ? launch_spmv_variant<VT, XT, WP, true, false>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, false>(a, max_blocks, s);
 }
 
 template <class VT, class XT>

@@ -1,0 +1,56 @@
+"""Autotuner: host-side candidate logic (CPU) and a tuned batch on the GPU that
+multiplies exactly like the untuned one and feeds the CG solver."""
+import numpy as np
+import pytest
+
+from paper_1507_08101_gb300 import autotune
+from workloads import generators as gen
+
+
+def test_lane_candidates():
+    assert autotune.lane_candidates(1, 4) == [1]
+    assert autotune.lane_candidates(8, 4) == [1, 2, 4, 8]
+    assert autotune.lane_candidates(6, 4) == [1, 2]
+    assert autotune.lane_candidates(3, 8) == [1]
+    assert autotune.lane_candidates(4, 8) == [1, 2, 4]
+    for w in range(1, 9):
+        for xs in (4, 8):
+            for c in autotune.lane_candidates(w, xs):
+                assert w % c == 0 and (w * xs) % min(16, c * xs) == 0
+
+
+def test_signature_is_structural():
+    a = gen.laplace2d(20)
+    b = gen.laplace2d(20, shift=5.0)  # same pattern, other values
+    c = gen.laplace2d(21)
+    assert autotune.signature(a, 2, "f32") == autotune.signature(b, 2, "f32")
+    assert autotune.signature(a, 2, "f32") != autotune.signature(a, 3, "f32")
+    assert autotune.signature(a, 2, "f32") != autotune.signature(c, 2, "f32")
+
+
+@pytest.mark.gpu
+def test_tuned_batch_runs_and_caches(cuda_ok, tmp_path):
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    mats = [gen.laplace2d(s, 0.01) for s in (40, 64, 40)]
+    widths = [2, 5, 2]
+    cache = str(tmp_path / "tune.json")
+    cfg = autotune.tune_batch(mats, widths, cache_path=cache, reps=5, sigmas=(1, 32))
+    assert cfg[0] == cfg[2]  # same structure and width: tuned once
+    for c, w in zip(cfg, widths):
+        assert c["C"] in autotune.C_CANDIDATES and c["sigma"] in (1, 32) and w % c["cpl"] == 0
+    again = autotune.tune_batch(mats, widths, cache_path=cache, reps=5, sigmas=(1, 32))
+    assert again == cfg
+    S = [sellcs.SellMatrix(A, C=c["C"], sigma=c["sigma"], dtype="f32") for A, c in zip(mats, cfg)]
+    xs = [torch.rand(A.nrows, w, dtype=torch.float32, device="cuda") for A, w in zip(mats, widths)]
+    y1 = [torch.empty_like(x) for x in xs]
+    y2 = [torch.empty_like(x) for x in xs]
+    b1 = sellcs.Batch(S, widths, cols_per_lane=[c["cpl"] for c in cfg], vec_dtype="f32")
+    b1.bind(xs, y1)
+    b1.spmv()
+    b2 = sellcs.Batch(S, widths, vec_dtype="f32")
+    b2.bind(xs, y2)
+    b2.spmv()
+    torch.cuda.synchronize()
+    for a, b in zip(y1, y2):
+        assert torch.equal(a, b)
