@@ -74,7 +74,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     using AT = typename AccOf<VT, XT>::T;
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW;
+    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
     const int gl = lane % G, rw = lane / G;
     const int k0 = gl * CPL;
     const int nvalid = M.w - k0 < CPL ? M.w - k0 : CPL;

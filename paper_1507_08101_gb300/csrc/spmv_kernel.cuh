@@ -116,8 +116,37 @@ __device__ __forceinline__ float val_to_acc<float, __nv_bfloat16>(__nv_bfloat16 
     return __bfloat162float(v);
 }
 
+// Loads of the matrix stream (values, column indices): read once, so they
+// should not displace x from the caches.  SP_STREAM_NOALLOC selects the
+// read-only path without L1 allocation; otherwise the evict-first hint.
+#ifndef SP_STREAM_NOALLOC
+#define SP_STREAM_NOALLOC 0
+#endif
+#if SP_STREAM_NOALLOC
+__device__ __forceinline__ double ld_stream(const double *p) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
+    unsigned short v;
+    asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_bfloat16(v);
+}
+#else
 template <class T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+#endif
 
 // Epilogue arithmetic with every product and sum rounded on its own (no
 // contraction into fused multiply-adds), so that each kernel that applies the
@@ -203,6 +232,10 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
 }
 
 // Row sums t[c] = sum_j val(s,j) * x[col(s,j), k0 + c] for the row in one slot.
+// U value/index loads and U gathers are in flight per step; the last
+// (len mod U) entries are issued the same way under a predicate, so a short
+// row (fewer than U entries) costs one round trip, not one per entry.  The
+// products are added in the order j = 0, 1, ..., len - 1 in every case.
 template <class VT, class XT, class AT, int CPL, bool VEC, int U>
 __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                             int len, const XT *__restrict__ xk, int64_t xrs, int64_t xcs,
@@ -229,17 +262,26 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
             }
         }
     }
-    for (; j < len; ++j) {
-        int32_t cc = ld_stream(cp);
-        VT vv = ld_stream(vp);
-        vp += C;
-        cp += C;
-        if (nvalid > 0) {
-            XT xv[CPL];
-            load_cols<XT, CPL, VEC>(xk + (int64_t)cc * xrs, xcs, nvalid, xv);
-            AT v = val_to_acc<AT, VT>(vv);
+    const int rest = len - j;
+    if (rest > 0) {
+        int32_t cc[U];
+        VT vv[U];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+        for (int u = 0; u < U; ++u) {
+            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
+            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : VT(0);
+        }
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u < rest) {
+                    XT xv[CPL];
+                    load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+                    AT v = val_to_acc<AT, VT>(vv[u]);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                }
+            }
         }
     }
 }
@@ -316,7 +358,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : SP_MINB_
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
     constexpr int ROWS = R * kSpmvWarps;
-    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW;
+    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % G, rw = lane / G;
