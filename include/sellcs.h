@@ -298,6 +298,44 @@ SP_API int sp_cg_solve(sp_cg *cg, const double *const *b, double *const *x, cons
                        sp_cg_stats *stats, double *rel_res, void *stream);
 SP_API int sp_cg_destroy(sp_cg *cg, void *stream);
 
+/* ------------------------------------------------------------------ no-allocation variant */
+
+/*
+ * sp_spmv_noalloc -- the augmented product of sp_spmv for callers that cannot
+ * allocate device memory: for instance a process whose GPU memory is already
+ * held by another allocator (a framework's caching pool), or a code path where
+ * cudaMalloc and cudaFree are not allowed because they synchronise the device.
+ * The paper has no counterpart of this entry point.
+ *
+ * It allocates nothing, on the device or the host.  Every input and output is
+ * a plain device pointer owned by the caller:
+ *   val, col, chunkptr, slotlen, perm  the SELL-C-sigma arrays in the layout
+ *       sp_mat_export_sell describes (perm NULL: identity, i.e. sigma = 1);
+ *       val in val_dtype
+ *   nrows, ncols, C        matrix shape and chunk height (1..1024)
+ *   x (ncols x w), y (nrows x w), z (nrows x w, or NULL without the chain):
+ *       row-major with leading dimensions ldx, ldy, ldz, in vec_dtype
+ *   w                      block width, 0..SP_NOALLOC_MAX_W
+ *   flags, alpha, beta, gamma (host: 1 or w values), delta, eta, dot (device,
+ *       3*w doubles): as in sp_spmv (SP_SPMV_DOT_HOST is rejected)
+ * The scratch of the fused dot products is a static device array of
+ * 3 * SP_NOALLOC_MAX_W * SP_NOALLOC_MAX_BLOCKS doubles (1.5 MiB) plus a ticket,
+ * held by every GPU that loads this library until the process exits.  A block
+ * width above SP_NOALLOC_MAX_W is rejected (SP_ERR_UNSUPPORTED, with the reason
+ * in sp_last_error_detail).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call clears the ticket and
+ * shares the array, so calls that overlap on the GPU (different streams, no
+ * ordering) race and must not be issued.  Asynchronous on `stream`.
+ */
+#define SP_NOALLOC_MAX_W 32
+#define SP_NOALLOC_MAX_BLOCKS 2048
+SP_API int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_t *col, const int64_t *chunkptr,
+                           const int32_t *slotlen, const int32_t *perm, int64_t nrows, int64_t ncols, int32_t C,
+                           const void *x, int64_t ldx, void *y, int64_t ldy, void *z, int64_t ldz, int32_t w,
+                           sp_dtype vec_dtype, uint32_t flags, double alpha, double beta, const double *gamma,
+                           double delta, double eta, double *dot, void *stream);
+
 /* ------------------------------------------------------------------ device info */
 /* Streaming multiprocessor count of the current device (for grid sizing tests). */
 SP_API int sp_device_sm_count(int *count);

@@ -60,6 +60,7 @@ class sp_cg_stats_t(ct.Structure):
 
 
 SP_BATCH_MAX_W = 8
+SP_NOALLOC_MAX_W = 32
 
 
 class SpError(RuntimeError):
@@ -103,6 +104,8 @@ _SIGS = {
     "sp_cg_create": (I, [PP, I, P, P, P, P, P]),
     "sp_cg_solve": (I, [P, P, P, ct.POINTER(sp_cg_opts_t), ct.POINTER(sp_cg_stats_t), P, P]),
     "sp_cg_destroy": (I, [P, P]),
+    "sp_spmv_noalloc": (I, [P, I, P, P, P, P, I64, I64, I32, P, I64, P, I64, P, I64, I32, I, ct.c_uint32,
+                            ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.c_double, ct.c_double, P, P]),
 }
 
 
