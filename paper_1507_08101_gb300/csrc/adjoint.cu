@@ -24,6 +24,7 @@ struct SampledArgs {
     const int64_t *rowptr;
     int64_t nrows, nslots;
     int32_t C, w;
+    int32_t log2_tpr;  // threads per row (lanes splitting a row's entries)
     const void *x;  // ncols x w row-major (ld = w)
     const void *g;  // nrows x w row-major (ld = w)
     void *dvals;
@@ -34,16 +35,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_sampled(const __grid_constant_
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int ROWS = R * kSpmvWarps;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gl = lane % G, rw = lane / G;
+    const int lt = a.log2_tpr;
+    const int T = 1 << lt;
+    const int gl = lane % G;
+    const int tt = (lane / G) & (T - 1);
+    const int rw = (lane / G) >> lt;
+    const int Rr = R >> lt;
+    const int ROWS = Rr * kSpmvWarps;
     const int k0 = gl * CPL;
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const XT *__restrict__ x = (const XT *)a.x + k0;
     const XT *__restrict__ g = (const XT *)a.g + k0;
     XT *__restrict__ out = (XT *)a.dvals;
     for (int64_t base = (int64_t)blockIdx.x * ROWS; base < a.nslots; base += (int64_t)gridDim.x * ROWS) {
-        const int64_t s = base + warp * R + rw;
+        const int64_t s = base + warp * Rr + rw;
         // all lanes of a row group take the same branches (same slot)
         int64_t i = -1;
         int len = 0;
@@ -63,16 +69,19 @@ __global__ void __launch_bounds__(kSpmvThreads) k_sampled(const __grid_constant_
             for (int c = 0; c < CPL; ++c) gv[c] = XT(0);
         }
         const int64_t dst = i >= 0 ? a.rowptr[i] : 0;
-        // every lane of the warp runs the longest row of the warp so that the
+        // this lane's entries of the row: j = tt, tt + T, ...
+        const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
+        // every lane of the warp runs the longest share of the warp so that the
         // shuffles below always see the full warp
-        int maxlen = len;
+        int maxlen = len_t;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
-        const int32_t *cp = a.col + off;
-        for (int j = 0; j < maxlen; ++j) {
+        const int32_t *cp = a.col + off + (int64_t)tt * a.C;
+        const int64_t step = (int64_t)a.C << lt;
+        for (int q = 0; q < maxlen; ++q) {
             XT sum = XT(0);
-            if (j < len && nvalid > 0) {
-                int32_t cc = ld_stream(cp + (int64_t)j * a.C);
+            if (q < len_t && nvalid > 0) {
+                int32_t cc = ld_stream(cp + q * step);
                 XT xv[CPL];
                 load_cols<XT, CPL, VEC>(x + (int64_t)cc * a.w, 1, nvalid, xv);
 #pragma unroll
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_sampled(const __grid_constant_
             }
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (gl == 0 && j < len) out[dst + j] = sum;
+            if (gl == 0 && q < len_t) out[dst + tt + (int64_t)q * T] = sum;
         }
     }
 }
@@ -90,6 +99,8 @@ static int launch_sampled_variant(const SampledArgs &a, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int ROWS = (32 / G) * kSpmvWarps;
+    SampledArgs b = a;
+    b.log2_tpr = host_log2_tpr(a.C, G);
     static int occ = 0;
     if (occ == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sampled<XT, WP, VEC>, kSpmvThreads, 0) !=
@@ -100,11 +111,11 @@ static int launch_sampled_variant(const SampledArgs &a, cudaStream_t s) {
     }
     int sms = 1;
     SP_TRY(device_sm_count(&sms));
-    int64_t need = (a.nslots + ROWS - 1) / ROWS;
+    int64_t need = ((a.nslots << b.log2_tpr) + ROWS - 1) / ROWS;
     int64_t grid = (int64_t)sms * occ;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_sampled<XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(a);
+    k_sampled<XT, WP, VEC><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

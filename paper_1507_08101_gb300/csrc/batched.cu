@@ -55,7 +55,8 @@ struct BMat {
 };
 
 struct BUnit {
-    int32_t m, variant;
+    int32_t m;
+    int16_t variant, log2_tpr;  // lane layout and threads per row of matrix m
     int64_t s0, s1;
 };
 
@@ -75,7 +76,13 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
     constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
-    const int gl = lane % G, rw = lane / G;
+    const int lt = u.log2_tpr;
+    const int T = 1 << lt;
+    const int gl = lane % G;
+    const int tt = (lane / G) & (T - 1);
+    const int rw = (lane / G) >> lt;
+    const int Rr = R >> lt;
+    const unsigned rowmask = (G * T == 32) ? 0xffffffffu : (((1u << (G * T)) - 1u) << (rw * G * T));
     const int k0 = gl * CPL;
     const int nvalid = M.w - k0 < CPL ? M.w - k0 : CPL;
     const uint32_t f = a.flags;
@@ -87,16 +94,23 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     double dyy[CPL], dxy[CPL], dxx[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) dyy[c] = dxy[c] = dxx[c] = 0.0;
-    for (int64_t s = u.s0 + rw; s < u.s1; s += R) {
+    for (int64_t s = u.s0 + rw; s < u.s1; s += Rr) {
         const int64_t i = M.perm ? (int64_t)M.perm[s] : (s < M.nrows ? s : -1);
         if (i < 0) continue;
         const uint32_t cidx = (uint32_t)s / (uint32_t)M.C;
-        const int64_t off = M.chunkptr[cidx] + ((uint32_t)s - cidx * (uint32_t)M.C);
+        const int64_t off = M.chunkptr[cidx] + ((uint32_t)s - cidx * (uint32_t)M.C) + (int64_t)tt * M.C;
         const int len = M.slotlen[s];
+        const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
         AT acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-        row_product<VT, XT, AT, CPL, true, U>(val + off, M.col + off, M.C, len, xk, M.w, 1, nvalid, acc);
+        row_product<VT, XT, AT, CPL, true, U>(val + off, M.col + off, M.C << lt, len_t, xk, M.w, 1, nvalid, acc);
+        if (T > 1) {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+                for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
+            if (tt != 0) continue;
+        }
         if (nvalid <= 0) continue;
         XT xi[CPL], yo[CPL], t[CPL];
         if (need_xi) load_cols<XT, CPL, true>(xk + i * M.w, 1, nvalid, xi);
@@ -216,7 +230,8 @@ static int make_units(Batch &B, int64_t target) {
             cost += (int64_t)(sl[s] + (s < P.nrows ? 2 : 0)) * std::max(1, w);
             bool cut = ((s + 1) % 32 == 0) && cost >= target;
             if (cut || s + 1 == P.nslots) {
-                B.hunits.push_back(BUnit{m, v, s0, s + 1});
+                int G = variant_wp(v) / variant_cpl(v);
+                B.hunits.push_back(BUnit{m, (int16_t)v, (int16_t)host_log2_tpr(P.C, G), s0, s + 1});
                 s0 = s + 1;
                 cost = 0;
             }

@@ -63,6 +63,7 @@ struct SpmvArgs {
     unsigned *ticket;
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
     int32_t nsm;             // SMs the grid was sized for
+    int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
     const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
     double gamma[kMaxTileW];
 };
@@ -78,8 +79,13 @@ struct SpmvArgs {
 #ifndef SP_MINB_W1
 #define SP_MINB_W1 1
 #endif
-#ifndef SP_MINB_WIDE
-#define SP_MINB_WIDE 1
+// minimum resident blocks per SM requested for wide blocks (WP >= 8):
+// measured best at 3 (float64 vectors) and 4 (float32 vectors)
+#ifndef SP_MINB_WIDE_F64
+#define SP_MINB_WIDE_F64 3
+#endif
+#ifndef SP_MINB_WIDE_F32
+#define SP_MINB_WIDE_F32 4
 #endif
 
 template <class VT, class XT>
@@ -107,6 +113,19 @@ inline int host_cols_per_lane(size_t xsize, int w) {
     while (wp < w) wp <<= 1;
     int c = xsize == 8 ? SP_CPL_MAX_F64 : SP_CPL_MAX_F32;
     return c < wp ? c : wp;
+}
+
+// Threads per row.  A chunk of C rows is read by C*T lanes when
+// C * T * G = 32: lane (r, t) takes the entries j = t, t + T, t + 2T, ... of
+// row r, so for each step the warp's value and index loads are one
+// contiguous run of 32 entries (T rows' worth of chunk columns); long rows
+// get T lanes each.  For C >= 32 / G (or C not a power of two) T = 1.
+inline int host_log2_tpr(int C, int G) {
+    int rows_t1 = 32 / G;
+    if (C >= rows_t1 || (C & (C - 1)) != 0) return 0;
+    int t = rows_t1 / C, l = 0;
+    while ((1 << l) < t) ++l;
+    return l;
 }
 
 template <class AT, class VT>
@@ -351,17 +370,22 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 #endif
 
 template <class VT, class XT, int WP, bool VEC, bool DOTS>
-__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : SP_MINB_WIDE))
+__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int ROWS = R * kSpmvWarps;
     constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gl = lane % G, rw = lane / G;
+    const int lt = a.log2_tpr;              // T = 1 << lt lanes per row (runtime)
+    const int T = 1 << lt;
+    const int gl = lane % G;
+    const int tt = (lane / G) & (T - 1);    // this lane's share of the row's entries
+    const int rw = (lane / G) >> lt;        // row of the warp
+    const int Rr = R >> lt;                 // rows per warp
+    const unsigned rowmask = (G * T == 32) ? 0xffffffffu : (((1u << (G * T)) - 1u) << (rw * G * T));
     const int k0 = gl * CPL;
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const uint32_t f = a.flags;
@@ -393,7 +417,16 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : SP_MINB_
         AT acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-        row_product<VT, XT, AT, CPL, VEC, U>(val + off, a.col + off, a.C, len, xk, a.xrs, a.xcs, nvalid, acc);
+        const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
+        row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
+                                             a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
+        if (T > 1) {
+            // combine the T partial sums of the row (fixed xor tree)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+                for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
+            if (tt != 0) return;
+        }
         if (nvalid <= 0) return;
         XT xi[CPL], yo[CPL], t[CPL];
         if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
@@ -441,10 +474,11 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : SP_MINB_
         const int64_t s0 = (int64_t)a.wbounds[gw] * 32;
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
-        for (int64_t s = s0 + rw; s < s1; s += R) slot(s);
+        for (int64_t s = s0 + rw; s < s1; s += Rr) slot(s);
     } else {
-        for (int64_t base = (int64_t)blockIdx.x * ROWS; base < a.nslots; base += (int64_t)gridDim.x * ROWS) {
-            const int64_t s = base + warp * R + rw;
+        const int rows = Rr * kSpmvWarps;
+        for (int64_t base = (int64_t)blockIdx.x * rows; base < a.nslots; base += (int64_t)gridDim.x * rows) {
+            const int64_t s = base + warp * Rr + rw;
             if (s < a.nslots) slot(s);
         }
     }

@@ -36,7 +36,8 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     }
     int sms = 1;
     SP_TRY(device_sm_count(&sms));
-    int64_t need = (a.nslots + ROWS - 1) / ROWS;
+    const int lt = host_log2_tpr(a.C, G);
+    int64_t need = ((a.nslots << lt) + ROWS - 1) / ROWS;
     int64_t grid = (int64_t)sms * occ;
     if (grid > max_blocks) grid = max_blocks;
     if (grid > need) grid = need;
@@ -44,6 +45,7 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     SpmvArgs b = a;
     b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid) : nullptr;
     b.nsm = sms;
+    b.log2_tpr = lt;
     k_spmmv<VT, XT, WP, VEC, DOTS><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;

@@ -129,3 +129,10 @@ def test_powerlaw_full_size_fp32(cuda_ok):
     ref_dv = oracle.sampled_product(A, G, X)
     s_dv = oracle.sampled_product(A, np.abs(G), np.abs(X)) + np.abs(ref_dv)
     assert_close(vals.grad.double().cpu().numpy(), ref_dv, s_dv, 1.1 * 10 * U32, "dvals")
+
+
+@pytest.mark.parametrize("C", [1, 4, 8])
+def test_adjoint_threads_per_row(cuda_ok, C):
+    A = gen.powerlaw(5000, seed=15)
+    for w, xdt in ((1, "f64"), (4, "f32"), (2, "f64")):
+        check_adjoint(A, w, C, 5000, xdt, seed=C)

@@ -169,3 +169,14 @@ def test_dot_to_host_pointer(cuda_ok, irregular):
     assert np.all(np.isnan(host[3:6]))
     sellcs.sp_dense_destroy(hx)
     sellcs.sp_dense_destroy(hy)
+
+
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
+def test_threads_per_row_long_rows(cuda_ok, C):
+    """Small C gives each row T = 32 / (C * lanes per row) lanes (long power-law rows)."""
+    A = gen.powerlaw(6000, seed=14)
+    mat = sellcs.SellMatrix(A, C=C, sigma=6000)
+    for w in (1, 2, 3, 4, 8):
+        run_case(A, C, 6000, w, ALL, mat=mat, seed=w)
+    for vdt, xdt in (("f32", "f32"), ("bf16", "f32")):
+        run_case(A, C, 64, 4, ALL, vdt=vdt, xdt=xdt)
