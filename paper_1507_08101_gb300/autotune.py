@@ -35,13 +35,14 @@ def signature(A, w: int, dtype: str) -> str:
 
 
 def lane_candidates(w: int, xsize: int):
-    """Columns per lane that divide w and keep every row 8/16-byte aligned."""
+    """Columns per lane that divide w, keep every row 8/16-byte aligned and do
+    not exceed the batched kernel's widest lane (2 doubles or 4 floats)."""
     wp = 1
     while wp < w:
         wp <<= 1
     out = []
     c = 1
-    while c <= min(wp, sellcs.SP_BATCH_MAX_W):
+    while c <= min(wp, 2 if xsize == 8 else 4):
         if w % c == 0 and (w * xsize) % min(16, c * xsize) == 0:
             out.append(c)
         c <<= 1

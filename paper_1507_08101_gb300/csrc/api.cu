@@ -37,7 +37,7 @@ int device_sm_count(int *n) {
 // 8 resident blocks per SM (2048 threads / 256) and 3 x 32 values, plus the
 // arrival ticket.
 int spmv_scratch_need(int sm_count, size_t *bytes, int *max_blocks) {
-    int mb = sm_count * (2048 / kSpmvThreads);
+    int mb = sm_count * (2048 / kMainThreads);
     *max_blocks = mb;
     *bytes = (size_t)mb * 3 * kMaxTileW * sizeof(double) + 256;
     return SP_OK;

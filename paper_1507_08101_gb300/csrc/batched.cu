@@ -156,8 +156,18 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     }
 }
 
+// widest lane vector a batch may use: 2 doubles or 4 floats (wider blocks use
+// more lanes per row); this bounds the registers of the one kernel that holds
+// every layout
+__host__ __device__ constexpr int batch_max_cpl(int xsize) { return xsize == 8 ? 2 : 4; }
+
+// minimum resident blocks per SM requested for the batched kernel (knob)
+#ifndef SP_BATCH_MINB
+#define SP_BATCH_MINB 1
+#endif
+
 template <class VT, class XT>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmmv_batched(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kSpmvThreads, SP_BATCH_MINB) k_spmmv_batched(const __grid_constant__ BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
     const int T = gridDim.x * kSpmvWarps;
@@ -165,17 +175,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmmv_batched(const __grid_con
         const BUnit U = a.units[u];
         const BMat M = a.mats[U.m];
         double *part = a.partials + (int64_t)u * 3 * kBatchMaxW;
+        constexpr bool wide = batch_max_cpl(sizeof(XT)) >= 4;
         switch (U.variant) {
             case 0: batch_unit<VT, XT, 1, 1>(a, M, U, lane, part); break;
             case 1: batch_unit<VT, XT, 2, 1>(a, M, U, lane, part); break;
             case 2: batch_unit<VT, XT, 2, 2>(a, M, U, lane, part); break;
             case 3: batch_unit<VT, XT, 4, 1>(a, M, U, lane, part); break;
             case 4: batch_unit<VT, XT, 4, 2>(a, M, U, lane, part); break;
-            case 5: batch_unit<VT, XT, 4, 4>(a, M, U, lane, part); break;
             case 6: batch_unit<VT, XT, 8, 1>(a, M, U, lane, part); break;
             case 7: batch_unit<VT, XT, 8, 2>(a, M, U, lane, part); break;
-            case 8: batch_unit<VT, XT, 8, 4>(a, M, U, lane, part); break;
-            default: batch_unit<VT, XT, 8, 8>(a, M, U, lane, part); break;
+            default:
+                if constexpr (wide) {
+                    if (U.variant == 5) batch_unit<VT, XT, 4, 4>(a, M, U, lane, part);
+                    else batch_unit<VT, XT, 8, 4>(a, M, U, lane, part);
+                }
+                break;
         }
     }
 }
@@ -248,7 +262,7 @@ static size_t xsize(sp_dtype t) { return t == SP_F64 ? 8 : 4; }
 static int auto_cpl(int w, size_t xs) {
     int wp = 1;
     while (wp < w) wp <<= 1;
-    int c = std::min(wp, (int)(16 / xs) * 2);
+    int c = std::min(wp, batch_max_cpl((int)xs));
     while (c > 1 && (w % c != 0 || ((size_t)w * xs) % std::min<size_t>(16, c * xs) != 0)) c >>= 1;
     return c;
 }
@@ -270,7 +284,8 @@ static int batch_init(Batch &B, int count, sp_mat *const *A, const int32_t *widt
         int c = (cpl && cpl[m] > 0) ? cpl[m] : auto_cpl(w, xsize(xdt));
         int wp = 1;
         while (wp < w) wp <<= 1;
-        if (c > wp || (w % c) != 0 || ((size_t)w * xsize(xdt)) % std::min<size_t>(16, c * xsize(xdt)) != 0)
+        if (c > wp || c > batch_max_cpl((int)xsize(xdt)) || (w % c) != 0 ||
+            ((size_t)w * xsize(xdt)) % std::min<size_t>(16, c * xsize(xdt)) != 0)
             return SP_ERR_ARG;
         int v = variant_of(wp, c);
         if (v < 0) return SP_ERR_ARG;

@@ -141,11 +141,13 @@ int device_sm_count(int *n);
 int build_partition(Pattern &P, cudaStream_t s);
 constexpr int kPartWarps = 8;  // warps per block of the partitioned kernels
 constexpr int kMaxOcc = 8;     // resident blocks per SM covered by the partition table
-// Partition table for a grid of `grid` blocks, or null when the grid is not
-// SMs * b for b <= kMaxOcc (then the kernels fall back to a block-strided loop).
-inline const int32_t *partition_for(const Pattern &P, int64_t grid) {
-    if (!P.bounds || P.bounds_sms <= 0 || grid % P.bounds_sms) return nullptr;
-    int64_t b = grid / P.bounds_sms;
+// Partition table for a grid of `warps` resident warps, or null when that is
+// not kPartWarps * b * SMs for b <= kMaxOcc (then the kernels fall back to a
+// block-strided loop).
+inline const int32_t *partition_for(const Pattern &P, int64_t warps) {
+    int64_t unit = (int64_t)kPartWarps * P.bounds_sms;
+    if (!P.bounds || P.bounds_sms <= 0 || warps % unit) return nullptr;
+    int64_t b = warps / unit;
     if (b < 1 || b > kMaxOcc) return nullptr;
     return (const int32_t *)P.bounds->ptr + P.bounds_off[b];
 }

@@ -35,8 +35,15 @@
 
 namespace sp {
 
-constexpr int kSpmvThreads = 256;
+constexpr int kSpmvThreads = 256;  // batched and sampled kernels
 constexpr int kSpmvWarps = kSpmvThreads / 32;
+// Block size of the main product kernel (warps per block, compile-time knob).
+// Larger blocks put more of one SM's warps on adjacent partition ranges.
+#ifndef SP_BLOCK_WARPS
+#define SP_BLOCK_WARPS 8
+#endif
+constexpr int kMainWarps = SP_BLOCK_WARPS;
+constexpr int kMainThreads = 32 * kMainWarps;
 constexpr int kMaxTileW = 32;
 
 struct SpmvArgs {
@@ -310,7 +317,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
 template <int CPL, int G>
 __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&dyy)[CPL], double (&dxy)[CPL],
                                             double (&dxx)[CPL]) {
-    __shared__ double sred[kSpmvWarps][3][kMaxTileW];
+    __shared__ double sred[kMainWarps][3][kMaxTileW];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -340,7 +347,7 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
         int q = t / a.w, k = t - q * a.w;
         double s = 0.0;
 #pragma unroll
-        for (int wi = 0; wi < kSpmvWarps; ++wi) s += sred[wi][q][k];
+        for (int wi = 0; wi < kMainWarps; ++wi) s += sred[wi][q][k];
         a.partials[(int64_t)t * nb + blockIdx.x] = s;
     }
     __threadfence();
@@ -349,7 +356,7 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    for (int t = warp; t < nv; t += kSpmvWarps) {
+    for (int t = warp; t < nv; t += kMainWarps) {
         int q = t / a.w, k = t - q * a.w;
         if (!(a.flags & (SP_SPMV_DOT_YY << q))) continue;
         double s = 0.0;
@@ -369,8 +376,10 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 #define SP_SWIZZLE 0
 #endif
 
-template <class VT, class XT, int WP, bool VEC, bool DOTS>
-__global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
+// MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
+// kernel is compiled for T = 1 and carries none of the split-row logic.
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
+__global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
@@ -379,7 +388,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : WP < 8 ?
     constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lt = a.log2_tpr;              // T = 1 << lt lanes per row (runtime)
+    const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
     const int T = 1 << lt;
     const int gl = lane % G;
     const int tt = (lane / G) & (T - 1);    // this lane's share of the row's entries
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : WP < 8 ?
         const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
         row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
                                              a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
-        if (T > 1) {
+        if (MT && T > 1) {
             // combine the T partial sums of the row (fixed xor tree)
 #pragma unroll
             for (int c = 0; c < CPL; ++c)
@@ -467,16 +476,16 @@ __global__ void __launch_bounds__(kSpmvThreads, (WP == 1 ? SP_MINB_W1 : WP < 8 ?
 #if SP_SWIZZLE
         const int nsm = a.nsm, per = gridDim.x / nsm;
         const int bsw = (blockIdx.x % nsm) * per + blockIdx.x / nsm;
-        const int gw = bsw * kSpmvWarps + warp;
+        const int gw = bsw * kMainWarps + warp;
 #else
-        const int gw = blockIdx.x * kSpmvWarps + warp;
+        const int gw = blockIdx.x * kMainWarps + warp;
 #endif
         const int64_t s0 = (int64_t)a.wbounds[gw] * 32;
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
         for (int64_t s = s0 + rw; s < s1; s += Rr) slot(s);
     } else {
-        const int rows = Rr * kSpmvWarps;
+        const int rows = Rr * kMainWarps;
         for (int64_t base = (int64_t)blockIdx.x * rows; base < a.nslots; base += (int64_t)gridDim.x * rows) {
             const int64_t s = base + warp * Rr + rw;
             if (s < a.nslots) slot(s);

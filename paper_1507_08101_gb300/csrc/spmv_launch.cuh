@@ -17,18 +17,18 @@ namespace sp {
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, bool DOTS>
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
-    constexpr int ROWS = (32 / G) * kSpmvWarps;
+    constexpr int ROWS = (32 / G) * kMainWarps;
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS>,
-                                                                      kSpmvThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT>,
+                                                                      kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
             occ = 1;
@@ -36,29 +36,37 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     }
     int sms = 1;
     SP_TRY(device_sm_count(&sms));
-    const int lt = host_log2_tpr(a.C, G);
+    const int lt = MT ? host_log2_tpr(a.C, G) : 0;
     int64_t need = ((a.nslots << lt) + ROWS - 1) / ROWS;
     int64_t grid = (int64_t)sms * occ;
     if (grid > max_blocks) grid = max_blocks;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     SpmvArgs b = a;
-    b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid) : nullptr;
+    b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
     b.nsm = sms;
     b.log2_tpr = lt;
-    k_spmmv<VT, XT, WP, VEC, DOTS><<<(unsigned)grid, kSpmvThreads, 0, s>>>(b);
+    k_spmmv<VT, XT, WP, VEC, DOTS, MT><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
-template <class VT, class XT, int WP>
-static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+template <class VT, class XT, int WP, bool MT>
+static int launch_spmv_wm(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     const bool dots = (a.flags & SP_SPMV_DOT_ANY) != 0;
     if (dots)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, true>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, true>(a, max_blocks, s);
-    return vec ? launch_spmv_variant<VT, XT, WP, true, false>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false, false>(a, max_blocks, s);
+        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, true, MT>(a, max_blocks, s);
+    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, false, MT>(a, max_blocks, s);
+}
+
+template <class VT, class XT, int WP>
+static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+    constexpr int CPL = cols_per_lane<XT, WP>();
+    const bool mt = host_log2_tpr(a.C, WP / CPL) > 0;
+    return mt ? launch_spmv_wm<VT, XT, WP, true>(a, vec, max_blocks, s)
+              : launch_spmv_wm<VT, XT, WP, false>(a, vec, max_blocks, s);
 }
 
 template <class VT, class XT>
