@@ -447,7 +447,7 @@ def secondary_cg_batch(peak):
     Bs = [B for _, B in batch]
     widths = [B.shape[1] for B in Bs]
     t0 = _t.time()
-    cfg = autotune.tune_batch(mats, widths, dtype="f32", vec_dtype="f32",
+    cfg = autotune.tune_batch_joint(mats, widths, dtype="f32", vec_dtype="f32",
                               cache_path=os.path.join(ROOT, "_autotune_cache.json"))
     tune_s = _t.time() - t0
     S64 = [sellcs.SellMatrix(A, C=c["C"], sigma=c["sigma"], dtype="f64") for A, c in zip(mats, cfg)]

@@ -1,10 +1,12 @@
 """Autotuner of the batched SpMMV launch configuration.
 
-For every matrix of a batch it picks the SELL chunk height C, the sort window
-sigma and the lane layout (columns per lane CPL, hence G = WP / CPL threads per
-row) by timing the candidates on the GPU: each candidate matrix is built with
-sp_mat_create_csr and multiplied through a one-matrix sp_batch (the same
-kernel the batch runs), timed with CUDA events.  Results are cached in a JSON
+It picks the SELL chunk height C, the sort window sigma and the lane layout
+(columns per lane CPL, hence G = WP / CPL lanes per column group and, through C,
+the threads per row T) by timing candidates on the GPU with CUDA events:
+either jointly for a whole batch (:func:`tune_batch_joint`: every candidate
+batch is built with sp_mat_create_csr and multiplied by one sp_batch launch,
+the kernel the solver runs) or per matrix (:func:`tune_batch`: each matrix
+through a one-matrix sp_batch).  Results are cached in a JSON
 file under a structural signature of the matrix (size, nonzeros, row-length
 histogram) and the block width, so equal structures are tuned once.
 
@@ -87,16 +89,80 @@ def tune_matrix(A, w: int, dtype: str = "f32", vec_dtype: str = "f32", reps: int
     return best
 
 
-def tune_batch(mats, widths, dtype: str = "f32", vec_dtype: str = "f32", cache_path: str | None = DEFAULT_CACHE,
-               reps: int = 20, Cs=C_CANDIDATES, sigmas=SIGMA_CANDIDATES):
-    """Per-matrix {C, sigma, cpl, us}; cached by structural signature."""
-    cache = {}
+LANE_POLICIES = ("widest", "narrowest", "middle")
+
+
+def _policy_cpl(w: int, xsize: int, policy: str) -> int:
+    c = lane_candidates(w, xsize)
+    return c[-1] if policy == "widest" else (c[0] if policy == "narrowest" else c[len(c) // 2])
+
+
+def tune_batch_joint(mats, widths, dtype: str = "f32", vec_dtype: str = "f32",
+                     cache_path: str | None = DEFAULT_CACHE, reps: int = 20, Cs=C_CANDIDATES,
+                     sigmas=SIGMA_CANDIDATES):
+    """One (C, sigma, lane policy) for the whole batch, chosen by timing the
+    batched launch itself (what the solver runs), so small matrices whose solo
+    launches are latency-bound do not decide by noise.  Returns the per-matrix
+    list of {C, sigma, cpl, us} (us: the batch time)."""
+    import torch
+    key = "batch:" + hashlib.sha1("|".join(signature(A, w, dtype) for A, w in zip(mats, widths)).encode()
+                                  ).hexdigest()[:20]
+    cache = _load_cache(cache_path)
+    if key not in cache:
+        tdt = torch.float32 if vec_dtype == "f32" else torch.float64
+        xs = 4 if vec_dtype == "f32" else 8
+        xv = [torch.rand(A.ncols, w, dtype=tdt, device="cuda") for A, w in zip(mats, widths)]
+        yv = [torch.empty(A.nrows, w, dtype=tdt, device="cuda") for A, w in zip(mats, widths)]
+        best = None
+        for C in Cs:
+            for sigma in sigmas:
+                if 1 < sigma < C:
+                    continue
+                S = [sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=dtype) for A in mats]
+                for pol in LANE_POLICIES:
+                    cpl = [_policy_cpl(int(w), xs, pol) for w in widths]
+                    b = sellcs.Batch(S, widths, cols_per_lane=cpl, vec_dtype=vec_dtype)
+                    b.bind(xv, yv)
+                    us = _time_batch(b, reps)
+                    b.close()
+                    if best is None or us < best[0]:
+                        best = (us, C, sigma, pol)
+                for m in S:
+                    m.close()
+        us, C, sigma, pol = best
+        cache[key] = {"C": C, "sigma": sigma, "policy": pol, "us": round(us, 2)}
+        _store_cache(cache_path, cache)
+    e = cache[key]
+    xs = 4 if vec_dtype == "f32" else 8
+    return [{"C": e["C"], "sigma": e["sigma"], "cpl": _policy_cpl(int(w), xs, e["policy"]), "us": e["us"]}
+            for w in widths]
+
+
+def _load_cache(cache_path):
     if cache_path and os.path.exists(cache_path):
         try:
             with open(cache_path) as f:
-                cache = json.load(f)
+                return json.load(f)
         except (OSError, ValueError):
-            cache = {}
+            pass
+    return {}
+
+
+def _store_cache(cache_path, cache):
+    if not cache_path:
+        return
+    os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+    tmp = cache_path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=0, sort_keys=True)
+    os.replace(tmp, cache_path)
+
+
+def tune_batch(mats, widths, dtype: str = "f32", vec_dtype: str = "f32", cache_path: str | None = DEFAULT_CACHE,
+               reps: int = 20, Cs=C_CANDIDATES, sigmas=SIGMA_CANDIDATES):
+    """Per-matrix {C, sigma, cpl, us}, each matrix timed on its own; cached by
+    structural signature."""
+    cache = _load_cache(cache_path)
     out = []
     dirty = False
     for A, w in zip(mats, widths):
@@ -105,10 +171,6 @@ def tune_batch(mats, widths, dtype: str = "f32", vec_dtype: str = "f32", cache_p
             cache[key] = tune_matrix(A, int(w), dtype, vec_dtype, reps, Cs, sigmas)
             dirty = True
         out.append(cache[key])
-    if cache_path and dirty:
-        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
-        tmp = cache_path + f".{os.getpid()}.tmp"
-        with open(tmp, "w") as f:
-            json.dump(cache, f, indent=0, sort_keys=True)
-        os.replace(tmp, cache_path)
+    if dirty:
+        _store_cache(cache_path, cache)
     return out

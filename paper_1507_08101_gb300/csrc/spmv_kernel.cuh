@@ -40,7 +40,7 @@ constexpr int kSpmvWarps = kSpmvThreads / 32;
 // Block size of the main product kernel (warps per block, compile-time knob).
 // Larger blocks put more of one SM's warps on adjacent partition ranges.
 #ifndef SP_BLOCK_WARPS
-#define SP_BLOCK_WARPS 8
+#define SP_BLOCK_WARPS 32
 #endif
 constexpr int kMainWarps = SP_BLOCK_WARPS;
 constexpr int kMainThreads = 32 * kMainWarps;

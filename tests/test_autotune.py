@@ -55,3 +55,16 @@ def test_tuned_batch_runs_and_caches(cuda_ok, tmp_path):
     torch.cuda.synchronize()
     for a, b in zip(y1, y2):
         assert torch.equal(a, b)
+
+
+@pytest.mark.gpu
+def test_joint_tuning(cuda_ok, tmp_path):
+    mats = [gen.laplace2d(s, 0.01) for s in (30, 50, 70)]
+    widths = [1, 4, 8]
+    cfg = autotune.tune_batch_joint(mats, widths, cache_path=str(tmp_path / "j.json"), reps=5,
+                                    Cs=(16, 32), sigmas=(1, 32))
+    assert len({(c["C"], c["sigma"]) for c in cfg}) == 1
+    for c, w in zip(cfg, widths):
+        assert w % c["cpl"] == 0 and c["cpl"] <= 4
+    assert autotune.tune_batch_joint(mats, widths, cache_path=str(tmp_path / "j.json"), reps=5,
+                                     Cs=(16, 32), sigmas=(1, 32)) == cfg
