@@ -163,7 +163,7 @@ __host__ __device__ constexpr int batch_max_cpl(int xsize) { return xsize == 8 ?
 
 // minimum resident blocks per SM requested for the batched kernel (knob)
 #ifndef SP_BATCH_MINB
-#define SP_BATCH_MINB 3
+#define SP_BATCH_MINB 4
 #endif
 
 template <class VT, class XT>

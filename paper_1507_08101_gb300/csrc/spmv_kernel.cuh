@@ -375,6 +375,14 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 #ifndef SP_SWIZZLE
 #define SP_SWIZZLE 0
 #endif
+// Latency overlap in the slot loop: issue the epilogue's loads before the row
+// loop, and load the next slot's metadata while the current slot runs.
+#ifndef SP_EARLY_EPI
+#define SP_EARLY_EPI 1
+#endif
+#ifndef SP_PREFETCH_META
+#define SP_PREFETCH_META 1
+#endif
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
@@ -416,13 +424,34 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
 
     // one row slot: row sums, then y = alpha (t - gamma x_i) + beta y_i, dots, chain
-    auto slot = [&](int64_t s) {
-        const int64_t i = a.perm ? (int64_t)a.perm[s] : (s < a.nrows ? s : -1);
-        if (i < 0) return;
+    // Where a slot's row lives: its original row i (-1 for a padding row),
+    // the offset of its first entry and its length.  Three independent loads.
+    struct Meta {
+        int64_t i, off;
+        int len;
+    };
+    auto meta_of = [&](int64_t s) {
+        Meta m;
+        m.i = a.perm ? (int64_t)a.perm[s] : (s < a.nrows ? s : -1);
         const uint32_t cidx = (uint32_t)s / (uint32_t)a.C;
-        const int r = (int)((uint32_t)s - cidx * (uint32_t)a.C);
-        const int64_t off = a.chunkptr[cidx] + r;
-        const int len = a.slotlen[s];
+        m.off = a.chunkptr[cidx] + (int64_t)((uint32_t)s - cidx * (uint32_t)a.C);
+        m.len = a.slotlen[s];
+        return m;
+    };
+
+    auto slot = [&](const Meta &m) {
+        const int64_t i = m.i;
+        if (i < 0) return;
+        const int64_t off = m.off;
+        const int len = m.len;
+        // the epilogue's own loads (x_i, old y) go out before the row loop
+        const bool epi_lane = (!MT || tt == 0) && nvalid > 0;
+        XT xi[CPL], yo[CPL], t[CPL];
+        XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
+        if (SP_EARLY_EPI && epi_lane) {
+            if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
+            if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+        }
         AT acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
@@ -437,10 +466,10 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             if (tt != 0) return;
         }
         if (nvalid <= 0) return;
-        XT xi[CPL], yo[CPL], t[CPL];
-        if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
-        XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
-        if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+        if (!SP_EARLY_EPI) {
+            if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
+            if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+        }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             XT v = (XT)acc[c];
@@ -483,12 +512,25 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         const int64_t s0 = (int64_t)a.wbounds[gw] * 32;
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
-        for (int64_t s = s0 + rw; s < s1; s += Rr) slot(s);
+        int64_t s = s0 + rw;
+        if (SP_PREFETCH_META) {
+            // the next slot's metadata is loaded while this slot is computed
+            Meta cur{-1, 0, 0};
+            if (s < s1) cur = meta_of(s);
+            for (; s < s1; s += Rr) {
+                Meta nxt{-1, 0, 0};
+                if (s + Rr < s1) nxt = meta_of(s + Rr);
+                slot(cur);
+                cur = nxt;
+            }
+        } else {
+            for (; s < s1; s += Rr) slot(meta_of(s));
+        }
     } else {
         const int rows = Rr * kMainWarps;
         for (int64_t base = (int64_t)blockIdx.x * rows; base < a.nslots; base += (int64_t)gridDim.x * rows) {
             const int64_t s = base + warp * Rr + rw;
-            if (s < a.nslots) slot(s);
+            if (s < a.nslots) slot(meta_of(s));
         }
     }
     if constexpr (DOTS) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);

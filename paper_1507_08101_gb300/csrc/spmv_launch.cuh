@@ -11,6 +11,12 @@
 
 namespace sp {
 
+// Row order of the product kernel: 0 = static cost-balanced contiguous range
+// per warp; 1 = block-strided front (all warps near the same rows).
+#ifndef SP_ORDER
+#define SP_ORDER 0
+#endif
+
 // Preferred shared-memory carveout (percent of the unified L1/shared array
 // given to shared memory); negative: leave the driver's choice.
 #ifndef SP_CARVEOUT
@@ -40,10 +46,13 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     int64_t need = ((a.nslots << lt) + ROWS - 1) / ROWS;
     int64_t grid = (int64_t)sms * occ;
     if (grid > max_blocks) grid = max_blocks;
-    if (grid > need) grid = need;
+    // with a partition table the whole persistent grid runs (idle warps exit at
+    // once), so even a small matrix is spread over every SM
+    const bool part = SP_ORDER == 0 && a.wbounds_src && partition_for(*a.wbounds_src, grid * kMainWarps);
+    if (!part && grid > need) grid = need;
     if (grid < 1) grid = 1;
     SpmvArgs b = a;
-    b.wbounds = a.wbounds_src ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
+    b.wbounds = part ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
     b.nsm = sms;
     b.log2_tpr = lt;
     k_spmmv<VT, XT, WP, VEC, DOTS, MT><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
