@@ -119,7 +119,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
         for (int c = 0; c < CPL; ++c) {
             XT v = (XT)acc[c];
             if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
-            if (f & SP_SPMV_AXPBY) v = add_rn(v, mul_rn(beta, yo[c]));
+            if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
             t[c] = v;
         }
         store_out<XT, CPL, true>((XT *)M.y + i * M.w + k0, 1, nvalid, t);
@@ -127,9 +127,9 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 double td = (double)t[c], xd = need_xi ? (double)xi[c] : 0.0;
-                dyy[c] += td * td;
-                dxy[c] += xd * td;
-                dxx[c] += xd * xd;
+                if (f & SP_SPMV_DOT_YY) dyy[c] = fma_rn(td, td, dyy[c]);
+                if (f & SP_SPMV_DOT_XY) dxy[c] = fma_rn(xd, td, dxy[c]);
+                if (f & SP_SPMV_DOT_XX) dxx[c] = fma_rn(xd, xd, dxx[c]);
             }
         }
     }

@@ -32,6 +32,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "ffloat.cuh"
 
 namespace sp {
 
@@ -68,6 +69,7 @@ struct SpmvArgs {
     int32_t dot_stride, dot_off;
     double *partials;
     unsigned *ticket;
+    const float2 *ffval;     // float64 values split into float pairs (float-float row sums), or null
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
     int32_t nsm;             // SMs the grid was sized for
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
@@ -82,6 +84,10 @@ struct SpmvArgs {
 #endif
 #ifndef SP_UNROLL_WIDE
 #define SP_UNROLL_WIDE 2
+#endif
+// entries in flight per lane for float-float row sums (more registers per entry)
+#ifndef SP_UNROLL_FF
+#define SP_UNROLL_FF 4
 #endif
 #ifndef SP_MINB_W1
 #define SP_MINB_W1 1
@@ -164,6 +170,11 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
     asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ float2 ld_stream(const float2 *p) {
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
     unsigned short v;
     asm("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(v) : "l"(p));
@@ -174,15 +185,17 @@ template <class T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 #endif
 
-// Epilogue arithmetic with every product and sum rounded on its own (no
-// contraction into fused multiply-adds), so that each kernel that applies the
-// same epilogue to the same row sum gets the same bits.
+// Epilogue arithmetic written as explicit fused multiply-adds and rounded
+// products (never left to the compiler's contraction), so that each kernel
+// that applies the same epilogue to the same row sum gets the same bits, with
+// as few float64 instructions as the formula allows (GB300's float64 rate is
+// low enough to bound these kernels):
+//   y = alpha * fma(-gamma, x_i, t);  y = fma(beta, y_old, y)
+//   z = fma(eta, y, delta * z);       <.,.> accumulated with fma
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // Load CPL consecutive columns of one row of a block vector.
 // VEC: all CPL columns valid, unit column stride, address aligned to
@@ -312,6 +325,57 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
     }
 }
 
+// Row sums of a float64 matrix stored as float pairs, in float-float
+// arithmetic (see ffloat.cuh); same loop structure and entry order as
+// row_product.
+template <int CPL, bool VEC, int U>
+__device__ __forceinline__ void row_product_ff(const float2 *__restrict__ vp, const int32_t *__restrict__ cp, int C,
+                                               int len, const double *__restrict__ xk, int64_t xrs, int64_t xcs,
+                                               int nvalid, FFAcc (&acc)[CPL]) {
+    int j = 0;
+    for (; j + U <= len; j += U) {
+        int32_t cc[U];
+        float2 vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = ld_stream(cp + (int64_t)u * C);
+            vv[u] = ld_stream(vp + (int64_t)u * C);
+        }
+        vp += (int64_t)U * C;
+        cp += (int64_t)U * C;
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                double xv[CPL];
+                load_cols<double, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) ff_madd(acc[c], vv[u].x, vv[u].y, xv[c]);
+            }
+        }
+    }
+    const int rest = len - j;
+    if (rest > 0) {
+        int32_t cc[U];
+        float2 vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
+            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : make_float2(0.0f, 0.0f);
+        }
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u < rest) {
+                    double xv[CPL];
+                    load_cols<double, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) ff_madd(acc[c], vv[u].x, vv[u].y, xv[c]);
+                }
+            }
+        }
+    }
+}
+
 // Final step of the fused reductions: per-block partial sums, and the last
 // block to arrive adds them up in block order.
 template <int CPL, int G>
@@ -386,14 +450,17 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
+// FF: float64 row sums in float-float arithmetic from the split values
+// (VT = XT = double only).
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool FF = false>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
+    constexpr int U = FF ? (SP_UNROLL_FF / CPL > 1 ? SP_UNROLL_FF / CPL : 1)
+                         : (CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
@@ -452,18 +519,42 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
             if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
         }
-        AT acc[CPL];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
         const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
-        row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                             a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
-        if (MT && T > 1) {
-            // combine the T partial sums of the row (fixed xor tree)
+        XT rs[CPL];  // the row sums, in the vector precision
+        if constexpr (FF) {
+            FFAcc acc[CPL];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c)
-                for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
-            if (tt != 0) return;
+            for (int c = 0; c < CPL; ++c) ff_zero(acc[c]);
+            row_product_ff<CPL, VEC, U>(a.ffval + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
+                                        a.C << lt, len_t, (const double *)xk, a.xrs, a.xcs, nvalid, acc);
+            if (MT && T > 1) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+                    for (int o = G; o < G * T; o <<= 1) {
+                        const float bh = __shfl_xor_sync(rowmask, acc[c].hi, o);
+                        const float bl = __shfl_xor_sync(rowmask, acc[c].lo, o);
+                        const double bn = __shfl_xor_sync(rowmask, acc[c].nat, o);
+                        ff_add(acc[c], bh, bl, bn);
+                    }
+                if (tt != 0) return;
+            }
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) rs[c] = (XT)ff_value(acc[c]);
+        } else {
+            AT acc[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+            row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
+                                                 a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
+            if (MT && T > 1) {
+                // combine the T partial sums of the row (fixed xor tree)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+                    for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
+                if (tt != 0) return;
+            }
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) rs[c] = (XT)acc[c];
         }
         if (nvalid <= 0) return;
         if (!SP_EARLY_EPI) {
@@ -472,10 +563,10 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-            XT v = (XT)acc[c];
-            if (shift) v = sub_rn(v, mul_rn(gam[c], xi[c]));
+            XT v = rs[c];
+            if (shift) v = fma_rn(-gam[c], xi[c], v);
             if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
-            if (f & SP_SPMV_AXPBY) v = add_rn(v, mul_rn(beta, yo[c]));
+            if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
             t[c] = v;
         }
         store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
@@ -484,9 +575,9 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             for (int c = 0; c < CPL; ++c) {
                 if (c < nvalid) {
                     double td = (double)t[c], xd = need_xi ? (double)xi[c] : 0.0;
-                    dyy[c] += td * td;
-                    dxy[c] += xd * td;
-                    dxx[c] += xd * xd;
+                    if (f & SP_SPMV_DOT_YY) dyy[c] = fma_rn(td, td, dyy[c]);
+                    if (f & SP_SPMV_DOT_XY) dxy[c] = fma_rn(xd, td, dxy[c]);
+                    if (f & SP_SPMV_DOT_XX) dxx[c] = fma_rn(xd, xd, dxx[c]);
                 }
             }
         }
@@ -495,7 +586,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             XT *zp = z + i * a.zrs + (int64_t)k0 * a.zcs;
             load_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) zo[c] = add_rn(mul_rn(delta, zo[c]), mul_rn(eta, t[c]));
+            for (int c = 0; c < CPL; ++c) zo[c] = fma_rn(eta, t[c], mul_rn(delta, zo[c]));
             store_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
         }
     };

@@ -180,3 +180,40 @@ def test_threads_per_row_long_rows(cuda_ok, C):
         run_case(A, C, 6000, w, ALL, mat=mat, seed=w)
     for vdt, xdt in (("f32", "f32"), ("bf16", "f32")):
         run_case(A, C, 64, 4, ALL, vdt=vdt, xdt=xdt)
+
+
+def test_float64_split_ranges(cuda_ok):
+    """float64 row sums run in float-float arithmetic when every value can be
+    split; values or x entries outside the split range (huge, tiny, zero,
+    infinite) take the float64 path.  All must meet the float64 tolerance."""
+    rng = np.random.default_rng(21)
+    A = random_csr(3000, 3000, 0.01, rng)
+    # x with entries far outside [2^-40, 2^40], exact zeros and a few infinities
+    X = rng.uniform(-1, 1, (3000, 3))
+    X[::97, 0] = 1e60
+    X[::89, 1] = 3e-30
+    X[::83, 2] = 0.0
+    run_case(A, 32, 64, 3, {"scale", "axpby", "dot_xx"}, seed=1)  # in-range baseline
+    import oracle as orc
+    for vals in (A.val, A.val * 1e45):  # second: matrix values out of range -> no split
+        B = gen.CSR(A.nrows, A.ncols, A.rowptr, A.col, vals)
+        m = sellcs.SellMatrix(B, C=32, sigma=64)
+        x = to_dev(X)
+        y = torch.zeros_like(x)
+        sellcs.spmv(m, x, y)
+        torch.cuda.synchronize()
+        yr = orc.spmmv(B, X)[0]
+        s = orc.spmmv_scale(B, X)
+        assert np.all(np.abs(y.cpu().numpy() - yr) <= 1e-12 * s + 1e-300)
+    X[5, 0] = np.inf
+    m = sellcs.SellMatrix(A, C=32, sigma=64)
+    y = torch.zeros(3000, 3, dtype=torch.float64, device="cuda")
+    sellcs.spmv(m, to_dev(X), y)
+    yr = orc.spmmv(A, X)[0]
+    yg = y.cpu().numpy()
+    # a non-finite x entry reaches exactly the rows that use it (the oracle's
+    # compensated sum turns inf into nan, so compare finiteness only)
+    np.testing.assert_array_equal(np.isfinite(yg), np.isfinite(yr))
+    fin = np.isfinite(yr)
+    s = orc.spmmv_scale(A, np.where(np.isfinite(X), X, 0.0))
+    assert np.all(np.abs(yg[fin] - yr[fin]) <= 1e-12 * s[fin] + 1e-300)
