@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "spmv_kernel.cuh"
+#include "ffloat.cuh"
 
 namespace sp {
 
@@ -91,9 +92,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     const VT *__restrict__ val = (const VT *)M.val;
     const XT *__restrict__ xk = (const XT *)M.x + k0;
     const XT alpha = (XT)a.alpha, beta = (XT)a.beta;
-    double dyy[CPL], dxy[CPL], dxx[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) dyy[c] = dxy[c] = dxx[c] = 0.0;
+    DotAcc<XT> ayy[CPL], axy[CPL], axx[CPL];
     for (int64_t s = u.s0 + rw; s < u.s1; s += Rr) {
         const int64_t i = M.perm ? (int64_t)M.perm[s] : (s < M.nrows ? s : -1);
         if (i < 0) continue;
@@ -126,16 +125,19 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
         if (dots) {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
-                double td = (double)t[c], xd = need_xi ? (double)xi[c] : 0.0;
-                if (f & SP_SPMV_DOT_YY) dyy[c] = fma_rn(td, td, dyy[c]);
-                if (f & SP_SPMV_DOT_XY) dxy[c] = fma_rn(xd, td, dxy[c]);
-                if (f & SP_SPMV_DOT_XX) dxx[c] = fma_rn(xd, xd, dxx[c]);
+                if (f & SP_SPMV_DOT_YY) ayy[c].add(t[c], t[c]);
+                if (f & SP_SPMV_DOT_XY) axy[c].add(xi[c], t[c]);
+                if (f & SP_SPMV_DOT_XX) axx[c].add(xi[c], xi[c]);
             }
         }
     }
     if (!dots) return;
+    double dyy[CPL], dxy[CPL], dxx[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
+        dyy[c] = ayy[c].value();
+        dxy[c] = axy[c].value();
+        dxx[c] = axx[c].value();
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
             dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
@@ -363,7 +365,7 @@ struct CGCol {
     int32_t it, active;
 };
 struct OuterCol {
-    double bb, rel, scale;
+    double bb, rel, scale, norm;  // norm = ||r|| = 1 / scale (0 when inactive)
     int32_t active, pad;
 };
 struct VUnit {
@@ -377,7 +379,7 @@ struct CGVec {
 };
 
 __global__ void k_cg_scalars(const BMat *mats, const double *partials, int count, double inner_tol2,
-                             CGCol *st, double *coef) {
+                             CGCol *st, double *coef, float2 *coef_f) {
     const int m = blockIdx.x, lane = threadIdx.x & 31, k = threadIdx.x >> 5;
     const BMat M = mats[m];
     if (k >= M.w) return;
@@ -409,17 +411,27 @@ __global__ void k_cg_scalars(const BMat *mats, const double *partials, int count
     }
     coef[(m * kBatchMaxW + k) * 2 + 0] = alpha;
     coef[(m * kBatchMaxW + k) * 2 + 1] = beta;
+    coef_f[m * kBatchMaxW + k] = make_float2((float)alpha, (float)beta);
 }
 
 template <class T>
-__global__ void k_cg_update(const VUnit *units, int nunits, const CGVec *vec, const double *coef) {
+__global__ void k_cg_update(const VUnit *units, int nunits, const CGVec *vec, const double *coef,
+                            const float2 *coef_f) {
     for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
         const VUnit U = units[u];
         const CGVec V = vec[U.m];
         T *r = (T *)V.r, *s = (T *)V.s, *p = (T *)V.p, *q = (T *)V.q, *d = (T *)V.d;
         for (int64_t e = U.e0 + threadIdx.x; e < U.e1; e += blockDim.x) {
-            int k = (int)(e % U.w);
-            T alpha = (T)coef[(U.m * kBatchMaxW + k) * 2], beta = (T)coef[(U.m * kBatchMaxW + k) * 2 + 1];
+            const int k = (int)(e - U.e0) % U.w;  // units start on a row boundary
+            T alpha, beta;
+            if constexpr (sizeof(T) == 4) {
+                const float2 ab = coef_f[U.m * kBatchMaxW + k];  // no float64 conversion per element
+                alpha = ab.x;
+                beta = ab.y;
+            } else {
+                alpha = coef[(U.m * kBatchMaxW + k) * 2];
+                beta = coef[(U.m * kBatchMaxW + k) * 2 + 1];
+            }
             T pe = r[e] + beta * p[e];
             T qe = s[e] + beta * q[e];
             p[e] = pe;
@@ -442,6 +454,7 @@ __global__ void k_outer_scalars(const BMat *mats, const double *partials, int co
     o.rel = o.bb > 0.0 ? sqrt(rr / o.bb) : 0.0;
     o.active = o.rel > tol;
     o.scale = (o.active && rr > 0.0) ? 1.0 / sqrt(rr) : 0.0;
+    o.norm = o.scale != 0.0 ? sqrt(rr) : 0.0;
     CGCol &c = st[m * kBatchMaxW + k];
     c.it = 0;
     c.active = o.active;
@@ -455,7 +468,7 @@ __global__ void k_start_inner(const VUnit *units, int nunits, const CGVec *vec, 
         const CGVec V = vec[U.m];
         T *r = (T *)V.r, *p = (T *)V.p, *q = (T *)V.q, *d = (T *)V.d;
         for (int64_t e = U.e0 + threadIdx.x; e < U.e1; e += blockDim.x) {
-            int k = (int)(e % U.w);
+            const int k = (int)(e - U.e0) % U.w;  // units start on a row boundary
             double sc = oc[U.m * kBatchMaxW + k].scale;
             r[e] = (T)(V.r64[e] * sc);
             p[e] = T(0);
@@ -472,9 +485,9 @@ __global__ void k_x_update(const VUnit *units, int nunits, const CGVec *vec, con
         const CGVec V = vec[U.m];
         const T *d = (const T *)V.d;
         for (int64_t e = U.e0 + threadIdx.x; e < U.e1; e += blockDim.x) {
-            int k = (int)(e % U.w);
-            double sc = oc[U.m * kBatchMaxW + k].scale;
-            if (sc != 0.0) V.x[e] += (double)d[e] / sc;
+            const int k = (int)(e - U.e0) % U.w;  // units start on a row boundary
+            const double nr = oc[U.m * kBatchMaxW + k].norm;
+            V.x[e] = __fma_rn((double)d[e], nr, V.x[e]);  // x += ||r|| d
         }
     }
 }
@@ -501,7 +514,7 @@ struct sp_cg {
     Batch b64;                   // residual: x64 -> r64 (y0 = b)
     Batch b32, b64in;            // inner products (float32, or float64 when asked)
     std::vector<VUnit> hvunits;
-    DevBufPtr dvunits, dvec32, dvec64, vecs, cgcol, outer, coef;
+    DevBufPtr dvunits, dvec32, dvec64, vecs, cgcol, outer, coef, coef_f;
     std::vector<CGVec> hvec32, hvec64;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [inner f32, inner f64]
@@ -658,6 +671,7 @@ int sp_cg_create(sp_cg **out, int count, sp_mat *const *A, const int32_t *widths
     if (rc == SP_OK) rc = dev_alloc(cg->cgcol, count * kBatchMaxW * sizeof(CGCol), cs);
     if (rc == SP_OK) rc = dev_alloc(cg->outer, count * kBatchMaxW * sizeof(OuterCol), cs);
     if (rc == SP_OK) rc = dev_alloc(cg->coef, count * kBatchMaxW * 2 * sizeof(double), cs);
+    if (rc == SP_OK) rc = dev_alloc(cg->coef_f, count * kBatchMaxW * sizeof(float2), cs);
     if (rc != SP_OK) return fail(rc);
     cudaError_t e = cudaMemcpy(cg->dvunits->ptr, cg->hvunits.data(), cg->hvunits.size() * sizeof(VUnit),
                                cudaMemcpyHostToDevice);
@@ -683,15 +697,15 @@ static int cg_inner_iteration(sp_cg *cg, int f64, double inner_tol2, cudaStream_
     SP_TRY(batch_launch(B, SP_SPMV_DOT_XX | SP_SPMV_DOT_XY, 1.0, 0.0, s));
     k_cg_scalars<<<cg->count, 32 * kBatchMaxW, 0, s>>>((const BMat *)B.dmats->ptr, (const double *)B.partials->ptr,
                                                        cg->count, inner_tol2, (CGCol *)cg->cgcol->ptr,
-                                                       (double *)cg->coef->ptr);
+                                                       (double *)cg->coef->ptr, (float2 *)cg->coef_f->ptr);
     int nu = (int)cg->hvunits.size();
     int g = std::min(nu, cg->grid_vec);
     if (f64)
         k_cg_update<double><<<g, 256, 0, s>>>((const VUnit *)cg->dvunits->ptr, nu, (const CGVec *)cg->dvec64->ptr,
-                                              (const double *)cg->coef->ptr);
+                                              (const double *)cg->coef->ptr, (const float2 *)cg->coef_f->ptr);
     else
         k_cg_update<float><<<g, 256, 0, s>>>((const VUnit *)cg->dvunits->ptr, nu, (const CGVec *)cg->dvec32->ptr,
-                                             (const double *)cg->coef->ptr);
+                                             (const double *)cg->coef->ptr, (const float2 *)cg->coef_f->ptr);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

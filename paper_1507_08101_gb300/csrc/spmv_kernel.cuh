@@ -533,13 +533,35 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
                     for (int o = G; o < G * T; o <<= 1) {
                         const float bh = __shfl_xor_sync(rowmask, acc[c].hi, o);
                         const float bl = __shfl_xor_sync(rowmask, acc[c].lo, o);
-                        const double bn = __shfl_xor_sync(rowmask, acc[c].nat, o);
-                        ff_add(acc[c], bh, bl, bn);
+                        const int bb = __shfl_xor_sync(rowmask, (int)acc[c].bad, o);
+                        ff_add(acc[c], bh, bl, bb != 0);
                     }
                 if (tt != 0) return;
             }
+            bool bad = false;
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) rs[c] = (XT)ff_value(acc[c]);
+            for (int c = 0; c < CPL; ++c) {
+                rs[c] = (XT)ff_value(acc[c]);
+                bad |= acc[c].bad;
+            }
+            if (bad) {
+                // rare: an x entry outside the split range -- the whole row in float64
+                double r[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) r[c] = 0.0;
+                if (nvalid > 0)
+                    for (int j = 0; j < len; ++j) {
+                        const float2 v = a.ffval[off + (int64_t)j * a.C];
+                        const double av = (double)v.x + (double)v.y;
+                        double xv[CPL];
+                        load_cols<double, CPL, VEC>((const double *)xk + (int64_t)a.col[off + (int64_t)j * a.C] * a.xrs,
+                                                    a.xcs, nvalid, xv);
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) r[c] = __fma_rn(av, xv[c], r[c]);
+                    }
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) rs[c] = (XT)r[c];
+            }
         } else {
             AT acc[CPL];
 #pragma unroll
