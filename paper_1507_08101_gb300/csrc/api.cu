@@ -321,6 +321,7 @@ int sp_mat_info(const sp_mat *A, sp_mat_info_t *info) {
     info->sigma = P.sigma;
     info->val_dtype = A->vdt;
     info->has_transpose = A->transpose != nullptr;
+    info->ff_rowsums = A->ffval != nullptr;
     return SP_OK;
 }
 
