@@ -54,12 +54,11 @@ def algorithmic_bytes(nnz, nrows, ncols, nchunks, nslots, w, sv, sx, axpby, chai
 FP64_PEAK_TFLOPS = 1.25  # nominal dense float64 rate of a GB300 (no measured figure exists)
 
 
-def fp64_flops(nnz, nrows, w, ff, shift, scale, axpby, ndots, chain):
-    """float64 flops the product issues on the float64 pipe per call: the row
-    sums (2 per nonzero and column) unless they run in float-float, plus the
-    epilogue per row and column (fma = 2, mul = 1)."""
-    per = 2 * int(shift) + int(scale) + 2 * int(axpby) + 2 * ndots + 3 * int(chain) + (1 if ff else 0)
-    return (0 if ff else 2 * nnz * w) + per * nrows * w
+def fp64_flops(nnz, nrows, w, shift, scale, axpby, ndots, chain):
+    """float64 flops of one call: the row sums (2 per nonzero and column) and
+    the epilogue per row and column (fma = 2, mul = 1)."""
+    per = 2 * int(shift) + int(scale) + 2 * int(axpby) + 2 * ndots + 3 * int(chain)
+    return 2 * nnz * w + per * nrows * w
 
 
 def load_peaks():
@@ -252,19 +251,17 @@ def run_ours(args, rank, world):
 
     gbs = nbytes / (ms_step * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
-    ff = bool(info.get("ff_rowsums", 0))
-    flops = fp64_flops(A.nnz, A.nrows, 1, ff, True, True, True, 2, True)
+    flops = fp64_flops(A.nnz, A.nrows, 1, True, True, True, 2, True)
     tflops = flops / (ms_step * 1e-3) / 1e12
     hbm = {"bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
            "peak_kind": f"{peak_kind} copy bandwidth (burst)",
            "traffic": recorded_traffic("k_spmmv_irregular_augmented.md"),
-           "kernel": "k_spmmv<double,double,1,VEC,DOTS,!MT," + ("FF>" if ff else "native>"),
+           "kernel": "k_spmmv<double,double,1,VEC,DOTS,!MT>",
            "algorithmic_bytes_per_launch": nbytes}
     alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
            "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
            "peak_kind": "nominal float64 rate (1.25 TFLOP/s = 2 fma per SM per cycle at 2.07 GHz on 152 SMs)",
-           "fp64_flops_per_launch": flops,
-           "row_sums": "float-float on the FP32 pipes" if ff else "float64 fma"}
+           "fp64_flops_per_launch": flops}
     # the binding resource is the one closest to its ceiling; the other is reported beside it
     roof = dict(alu if alu["frac"] > hbm["frac"] else hbm)
     roof["other"] = hbm if roof["bound"] == "alu" else alu

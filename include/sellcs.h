@@ -120,7 +120,6 @@ typedef struct {
     int64_t sigma;
     sp_dtype val_dtype;
     int32_t has_transpose;
-    int32_t ff_rowsums; /* 1: float64 row sums run in float-float arithmetic (values split) */
 } sp_mat_info_t;
 
 SP_API int sp_mat_info(const sp_mat *A, sp_mat_info_t *info);

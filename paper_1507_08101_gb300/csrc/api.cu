@@ -12,7 +12,6 @@
 namespace sp {
 template <class VT, class XT>
 int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
-int launch_spmv_ff(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
 }
 
 static thread_local char g_detail[512] = "";
@@ -93,7 +92,6 @@ int launch_spmv(const SpmvLaunch &L, cudaStream_t s) {
     a.ticket = L.ticket;
     a.wbounds = nullptr;
     a.wbounds_src = L.P;
-    a.ffval = (L.vdt == SP_F64 && L.xdt == SP_F64) ? L.ffval : nullptr;
     for (int k = 0; k < kMaxTileW; ++k) a.gamma[k] = (L.gamma && k < L.w) ? L.gamma[k] : 0.0;
 
     size_t xs = dtype_size(L.xdt);
@@ -104,9 +102,7 @@ int launch_spmv(const SpmvLaunch &L, cudaStream_t s) {
     };
     bool vec = (L.w % cpl == 0) && aligned(L.x) && aligned(L.y) &&
                (!(L.flags & SP_SPMV_CHAIN_AXPBY) || aligned(L.z));
-    if (L.vdt == SP_F64 && L.xdt == SP_F64)
-        return a.ffval ? launch_spmv_ff(a, vec, L.max_blocks, s)
-                       : launch_spmv_typed<double, double>(a, vec, L.max_blocks, s);
+    if (L.vdt == SP_F64 && L.xdt == SP_F64) return launch_spmv_typed<double, double>(a, vec, L.max_blocks, s);
     if (L.vdt == SP_F32 && L.xdt == SP_F64) return launch_spmv_typed<float, double>(a, vec, L.max_blocks, s);
     if (L.vdt == SP_F32 && L.xdt == SP_F32) return launch_spmv_typed<float, float>(a, vec, L.max_blocks, s);
     if (L.vdt == SP_BF16 && L.xdt == SP_F64)
@@ -223,8 +219,6 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     A->vdt = val_dtype;
     int rc = build_pattern_and_values(A, nrows, ncols, prp, pcol, pval, f32, C, sigma, s);
     if (rc == SP_OK && (flags & SP_MAT_WITH_TRANSPOSE)) rc = build_transpose(A, prp, pcol, pval, f32, s);
-    if (rc == SP_OK) rc = build_ff_split(A, s);
-    if (rc == SP_OK && A->transpose) rc = build_ff_split(A->transpose, s);
     if (rc == SP_OK) rc = ensure_scratch(A, s);
     if (rc == SP_OK && A->transpose) rc = ensure_scratch(A->transpose, s);
     if (rc == SP_OK) {
@@ -259,14 +253,12 @@ int sp_mat_update_values(sp_mat *A, const void *val, unsigned flags, void *strea
         pv = tmp->ptr;
     }
     SP_TRY(fill_values_from_csr(*A->pat, A->vdt, A->val->ptr, pv, f32, s));
-    SP_TRY(build_ff_split(A, s));
     if (A->transpose) {
         const Pattern &T = *A->transpose->pat;
         DevBufPtr tv;
         SP_TRY(dev_alloc(tv, std::max<int64_t>(nnz, 1) * vs, s));
         SP_TRY(gather_values(pv, f32, (const int64_t *)T.src_index->ptr, nnz, tv->ptr, f32, s));
         SP_TRY(fill_values_from_csr(T, A->transpose->vdt, A->transpose->val->ptr, tv->ptr, f32, s));
-        SP_TRY(build_ff_split(A->transpose, s));
         // keep the temporary alive until the gather has run
         SP_CUDA(cudaStreamSynchronize(s));
     } else if (tmp) {
@@ -281,7 +273,6 @@ static int clone_one(sp_mat **out, const sp_mat *A, sp_dtype vdt, cudaStream_t s
     B->vdt = vdt;
     int rc = dev_alloc(B->val, A->pat->nstored * dtype_size(vdt), s);
     if (rc == SP_OK) rc = convert_values(A->val->ptr, A->vdt, B->val->ptr, vdt, A->pat->nstored, s);
-    if (rc == SP_OK) rc = build_ff_split(B, s);
     if (rc == SP_OK) rc = ensure_scratch(B, s);
     if (rc != SP_OK) {
         delete B;
@@ -321,7 +312,6 @@ int sp_mat_info(const sp_mat *A, sp_mat_info_t *info) {
     info->sigma = P.sigma;
     info->val_dtype = A->vdt;
     info->has_transpose = A->transpose != nullptr;
-    info->ff_rowsums = A->ffval != nullptr;
     return SP_OK;
 }
 
@@ -553,7 +543,6 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
     SpmvLaunch L;
     L.P = &P;
     L.val = A->val->ptr;
-    L.ffval = A->ffval ? (const float2 *)A->ffval->ptr : nullptr;
     L.vdt = A->vdt;
     L.xdt = x->dtype;
     L.flags = f & ~SP_SPMV_DOT_HOST;

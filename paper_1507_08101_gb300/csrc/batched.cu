@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "spmv_kernel.cuh"
-#include "ffloat.cuh"
+#include "dotacc.cuh"
 
 namespace sp {
 

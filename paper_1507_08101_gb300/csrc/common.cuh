@@ -71,7 +71,6 @@ struct sp_mat {
     sp::PatternPtr pat;
     sp_dtype vdt = SP_F64;
     sp::DevBufPtr val;           // vdt[nstored]
-    sp::DevBufPtr ffval;         // float64 values split into float pairs (float2[nstored]), or null
     sp_mat *transpose = nullptr; // owned
     // reduction scratch for the fused dot products (per-block partials + ticket)
     sp::DevBufPtr scratch;
@@ -110,9 +109,7 @@ int gather_values(const void *src, bool src_f32, const int64_t *index, int64_t n
                   bool dst_f32, cudaStream_t s);
 int convert_values(const void *src, sp_dtype sdt, void *dst, sp_dtype ddt, int64_t n, cudaStream_t s);
 int widen_values(const void *src, sp_dtype sdt, double *dst, int64_t n, cudaStream_t s);
-// (Re)build A->ffval from float64 values; leaves it null when any value is out
-// of the float-float range (then the float64 kernel runs).  Synchronises.
-int build_ff_split(sp_mat *A, cudaStream_t s);
+
 
 // ------------------------------------------------------------------ SpMMV launch
 struct VecDesc {
@@ -123,7 +120,6 @@ struct VecDesc {
 struct SpmvLaunch {
     const Pattern *P;
     const void *val;
-    const float2 *ffval;  // split float64 values, or null
     sp_dtype vdt, xdt;
     int w;
     VecDesc x, y, z;

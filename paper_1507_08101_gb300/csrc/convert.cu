@@ -16,7 +16,6 @@
 #include <vector>
 
 #include "common.cuh"
-#include "ffloat.cuh"
 
 namespace sp {
 
@@ -667,44 +666,6 @@ int convert_values(const void *src, sp_dtype sdt, void *dst, sp_dtype ddt, int64
 
 int widen_values(const void *src, sp_dtype sdt, double *dst, int64_t n, cudaStream_t s) {
     return convert_values(src, sdt, dst, SP_F64, n, s);
-}
-
-// ------------------------------------------------------------------ float-float split of float64 values
-
-__global__ void k_ff_split(const double *__restrict__ v, int64_t n, float2 *__restrict__ out, int *__restrict__ bad) {
-    int local_bad = 0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        float h, l;
-        if (!ff_split(v[q], h, l)) local_bad = 1;
-        out[q] = make_float2(h, l);
-    }
-    if (local_bad) atomicOr(bad, 1);
-}
-
-// Float-float row sums are used unless disabled at build time (SP_FF=0).
-#ifndef SP_FF
-#define SP_FF 1
-#endif
-
-int build_ff_split(sp_mat *A, cudaStream_t s) {
-    const Pattern &P = *A->pat;
-    if (!SP_FF || A->vdt != SP_F64 || P.nstored == 0) {
-        A->ffval.reset();
-        return SP_OK;
-    }
-    if (!A->ffval || A->ffval->bytes != (size_t)P.nstored * sizeof(float2))
-        SP_TRY(dev_alloc(A->ffval, P.nstored * sizeof(float2), s));
-    Tmp flag(s);
-    SP_TRY(flag.alloc(sizeof(int)));
-    SP_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-    k_ff_split<<<grid_for(P.nstored), kThreads, 0, s>>>((const double *)A->val->ptr, P.nstored,
-                                                       (float2 *)A->ffval->ptr, flag.as<int>());
-    SP_CUDA(cudaGetLastError());
-    int bad = 0;
-    SP_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SP_CUDA(cudaStreamSynchronize(s));
-    if (bad) A->ffval.reset();
-    return SP_OK;
 }
 
 }  // namespace sp

@@ -124,7 +124,6 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     a.dot_off = 0;
     a.partials = na->partials;
     a.ticket = na->ticket;
-    a.ffval = nullptr;  // the caller's float64 values are used as they are
     a.wbounds = nullptr;
     a.wbounds_src = nullptr;
     a.nsm = 0;

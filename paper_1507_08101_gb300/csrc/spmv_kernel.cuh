@@ -32,7 +32,6 @@
 #include <string.h>
 
 #include "common.cuh"
-#include "ffloat.cuh"
 
 namespace sp {
 
@@ -69,7 +68,6 @@ struct SpmvArgs {
     int32_t dot_stride, dot_off;
     double *partials;
     unsigned *ticket;
-    const float2 *ffval;     // float64 values split into float pairs (float-float row sums), or null
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
     int32_t nsm;             // SMs the grid was sized for
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
@@ -84,10 +82,6 @@ struct SpmvArgs {
 #endif
 #ifndef SP_UNROLL_WIDE
 #define SP_UNROLL_WIDE 2
-#endif
-// entries in flight per lane for float-float row sums (more registers per entry)
-#ifndef SP_UNROLL_FF
-#define SP_UNROLL_FF 4
 #endif
 #ifndef SP_MINB_W1
 #define SP_MINB_W1 1
@@ -168,11 +162,6 @@ __device__ __forceinline__ float ld_stream(const float *p) {
 __device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
     int32_t v;
     asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float2 ld_stream(const float2 *p) {
-    float2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
 }
 __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
@@ -325,57 +314,6 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
     }
 }
 
-// Row sums of a float64 matrix stored as float pairs, in float-float
-// arithmetic (see ffloat.cuh); same loop structure and entry order as
-// row_product.
-template <int CPL, bool VEC, int U>
-__device__ __forceinline__ void row_product_ff(const float2 *__restrict__ vp, const int32_t *__restrict__ cp, int C,
-                                               int len, const double *__restrict__ xk, int64_t xrs, int64_t xcs,
-                                               int nvalid, FFAcc (&acc)[CPL]) {
-    int j = 0;
-    for (; j + U <= len; j += U) {
-        int32_t cc[U];
-        float2 vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            cc[u] = ld_stream(cp + (int64_t)u * C);
-            vv[u] = ld_stream(vp + (int64_t)u * C);
-        }
-        vp += (int64_t)U * C;
-        cp += (int64_t)U * C;
-        if (nvalid > 0) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                double xv[CPL];
-                load_cols<double, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) ff_madd(acc[c], vv[u].x, vv[u].y, xv[c]);
-            }
-        }
-    }
-    const int rest = len - j;
-    if (rest > 0) {
-        int32_t cc[U];
-        float2 vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
-            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : make_float2(0.0f, 0.0f);
-        }
-        if (nvalid > 0) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (u < rest) {
-                    double xv[CPL];
-                    load_cols<double, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) ff_madd(acc[c], vv[u].x, vv[u].y, xv[c]);
-                }
-            }
-        }
-    }
-}
-
 // Final step of the fused reductions: per-block partial sums, and the last
 // block to arrive adds them up in block order.
 template <int CPL, int G>
@@ -450,17 +388,14 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
-// FF: float64 row sums in float-float arithmetic from the split values
-// (VT = XT = double only).
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool FF = false>
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int U = FF ? (SP_UNROLL_FF / CPL > 1 ? SP_UNROLL_FF / CPL : 1)
-                         : (CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL);
+    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
@@ -521,48 +456,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
         const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
         XT rs[CPL];  // the row sums, in the vector precision
-        if constexpr (FF) {
-            FFAcc acc[CPL];
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) ff_zero(acc[c]);
-            row_product_ff<CPL, VEC, U>(a.ffval + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                        a.C << lt, len_t, (const double *)xk, a.xrs, a.xcs, nvalid, acc);
-            if (MT && T > 1) {
-#pragma unroll
-                for (int c = 0; c < CPL; ++c)
-                    for (int o = G; o < G * T; o <<= 1) {
-                        const float bh = __shfl_xor_sync(rowmask, acc[c].hi, o);
-                        const float bl = __shfl_xor_sync(rowmask, acc[c].lo, o);
-                        const int bb = __shfl_xor_sync(rowmask, (int)acc[c].bad, o);
-                        ff_add(acc[c], bh, bl, bb != 0);
-                    }
-                if (tt != 0) return;
-            }
-            bool bad = false;
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-                rs[c] = (XT)ff_value(acc[c]);
-                bad |= acc[c].bad;
-            }
-            if (bad) {
-                // rare: an x entry outside the split range -- the whole row in float64
-                double r[CPL];
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) r[c] = 0.0;
-                if (nvalid > 0)
-                    for (int j = 0; j < len; ++j) {
-                        const float2 v = a.ffval[off + (int64_t)j * a.C];
-                        const double av = (double)v.x + (double)v.y;
-                        double xv[CPL];
-                        load_cols<double, CPL, VEC>((const double *)xk + (int64_t)a.col[off + (int64_t)j * a.C] * a.xrs,
-                                                    a.xcs, nvalid, xv);
-#pragma unroll
-                        for (int c = 0; c < CPL; ++c) r[c] = __fma_rn(av, xv[c], r[c]);
-                    }
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) rs[c] = (XT)r[c];
-            }
-        } else {
+        {
             AT acc[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);

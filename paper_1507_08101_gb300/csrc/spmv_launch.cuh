@@ -23,7 +23,7 @@ namespace sp {
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool FF = false>
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
@@ -31,9 +31,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT, FF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT, FF>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT>,
                                                                       kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -55,47 +55,39 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.wbounds = part ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
     b.nsm = sms;
     b.log2_tpr = lt;
-    k_spmmv<VT, XT, WP, VEC, DOTS, MT, FF><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
+    k_spmmv<VT, XT, WP, VEC, DOTS, MT><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
-template <class VT, class XT, int WP, bool MT, bool FF>
+template <class VT, class XT, int WP, bool MT>
 static int launch_spmv_wm(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     const bool dots = (a.flags & SP_SPMV_DOT_ANY) != 0;
     if (dots)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT, FF>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, true, MT, FF>(a, max_blocks, s);
-    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT, FF>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false, false, MT, FF>(a, max_blocks, s);
+        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, true, MT>(a, max_blocks, s);
+    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, false, MT>(a, max_blocks, s);
 }
 
-template <class VT, class XT, int WP, bool FF>
+template <class VT, class XT, int WP>
 static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     const bool mt = host_log2_tpr(a.C, WP / CPL) > 0;
-    return mt ? launch_spmv_wm<VT, XT, WP, true, FF>(a, vec, max_blocks, s)
-              : launch_spmv_wm<VT, XT, WP, false, FF>(a, vec, max_blocks, s);
-}
-
-template <class VT, class XT, bool FF>
-int launch_spmv_width(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
-    int w = a.w;
-    if (w <= 1) return launch_spmv_w<VT, XT, 1, FF>(a, vec, max_blocks, s);
-    if (w <= 2) return launch_spmv_w<VT, XT, 2, FF>(a, vec, max_blocks, s);
-    if (w <= 4) return launch_spmv_w<VT, XT, 4, FF>(a, vec, max_blocks, s);
-    if (w <= 8) return launch_spmv_w<VT, XT, 8, FF>(a, vec, max_blocks, s);
-    if (w <= 16) return launch_spmv_w<VT, XT, 16, FF>(a, vec, max_blocks, s);
-    if (w <= 32) return launch_spmv_w<VT, XT, 32, FF>(a, vec, max_blocks, s);
-    return SP_ERR_ARG;
+    return mt ? launch_spmv_wm<VT, XT, WP, true>(a, vec, max_blocks, s)
+              : launch_spmv_wm<VT, XT, WP, false>(a, vec, max_blocks, s);
 }
 
 template <class VT, class XT>
 int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
-    return launch_spmv_width<VT, XT, false>(a, vec, max_blocks, s);
+    int w = a.w;
+    if (w <= 1) return launch_spmv_w<VT, XT, 1>(a, vec, max_blocks, s);
+    if (w <= 2) return launch_spmv_w<VT, XT, 2>(a, vec, max_blocks, s);
+    if (w <= 4) return launch_spmv_w<VT, XT, 4>(a, vec, max_blocks, s);
+    if (w <= 8) return launch_spmv_w<VT, XT, 8>(a, vec, max_blocks, s);
+    if (w <= 16) return launch_spmv_w<VT, XT, 16>(a, vec, max_blocks, s);
+    if (w <= 32) return launch_spmv_w<VT, XT, 32>(a, vec, max_blocks, s);
+    return SP_ERR_ARG;
 }
-
-// float64 values and vectors with float-float row sums (a.ffval set)
-int launch_spmv_ff(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
 
 }  // namespace sp

@@ -40,7 +40,7 @@ DTYPES = {"f64": SP_F64, "f32": SP_F32, "bf16": SP_BF16}
 class sp_mat_info_t(ct.Structure):
     _fields_ = [("nrows", ct.c_int64), ("ncols", ct.c_int64), ("nnz", ct.c_int64), ("nchunks", ct.c_int64),
                 ("nstored", ct.c_int64), ("C", ct.c_int32), ("maxrowlen", ct.c_int32), ("sigma", ct.c_int64),
-                ("val_dtype", ct.c_int), ("has_transpose", ct.c_int32), ("ff_rowsums", ct.c_int32)]
+                ("val_dtype", ct.c_int), ("has_transpose", ct.c_int32)]
 
 
 class sp_spmv_opts(ct.Structure):
