@@ -90,6 +90,8 @@ int launch_spmv(const SpmvLaunch &L, cudaStream_t s) {
     a.dot_off = L.dot_off;
     a.partials = L.partials;
     a.ticket = L.ticket;
+    a.sched = nullptr;
+    a.sched_rounds = 0;
     a.wbounds = nullptr;
     a.wbounds_src = L.P;
     for (int k = 0; k < kMaxTileW; ++k) a.gamma[k] = (L.gamma && k < L.w) ? L.gamma[k] : 0.0;

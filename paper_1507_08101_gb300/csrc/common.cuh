@@ -62,6 +62,14 @@ struct Pattern {
     DevBufPtr bounds;    // int32
     int64_t bounds_off[9] = {0};
     int32_t bounds_sms = 0;
+    // Moving-front schedule (same grids): round r, warp t of the grid takes the
+    // 32-slot block sched[off[b] + r * warps + t] (-1: none).  In each round the
+    // blocks of the grid cover the next run of adjacent 32-slot blocks, each CTA
+    // a contiguous piece of it, assigned to the CTA's warps longest first to the
+    // least loaded so far.
+    DevBufPtr sched;     // int32
+    int64_t sched_off[9] = {0};
+    int32_t sched_rounds[9] = {0};
 };
 using PatternPtr = std::shared_ptr<Pattern>;
 
@@ -141,6 +149,7 @@ int launch_sampled(const Pattern &P, sp_dtype xdt, int w, const void *x, const v
 int device_sm_count(int *n);
 int build_partition(Pattern &P, cudaStream_t s);
 constexpr int kPartWarps = 8;  // warps per block of the partitioned kernels
+constexpr int kSchedCtaWarps = 32;  // warps per CTA the front schedule is built for
 constexpr int kMaxOcc = 8;     // resident blocks per SM covered by the partition table
 // Partition table for a grid of `warps` resident warps, or null when that is
 // not kPartWarps * b * SMs for b <= kMaxOcc (then the kernels fall back to a
@@ -151,6 +160,15 @@ inline const int32_t *partition_for(const Pattern &P, int64_t warps) {
     int64_t b = warps / unit;
     if (b < 1 || b > kMaxOcc) return nullptr;
     return (const int32_t *)P.bounds->ptr + P.bounds_off[b];
+}
+// Front schedule for a grid of `warps` resident warps in CTAs of kSchedCtaWarps, or null.
+inline const int32_t *schedule_for(const Pattern &P, int64_t warps, int *rounds) {
+    int64_t unit = (int64_t)kPartWarps * P.bounds_sms;
+    if (!P.sched || P.bounds_sms <= 0 || warps % unit) return nullptr;
+    int64_t b = warps / unit;
+    if (b < 1 || b > kMaxOcc || P.sched_rounds[b] <= 0) return nullptr;
+    *rounds = P.sched_rounds[b];
+    return (const int32_t *)P.sched->ptr + P.sched_off[b];
 }
 
 }  // namespace sp

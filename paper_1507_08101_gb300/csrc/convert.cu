@@ -425,6 +425,48 @@ int build_partition(Pattern &P, cudaStream_t s) {
         SP_CUDA(cudaGetLastError());
     }
     P.bounds_sms = sms;
+
+    // moving-front schedules, for the grids a kSchedCtaWarps-warp kernel runs
+    // (one or two resident CTAs per SM)
+    if (nb32 > 0) {
+        std::vector<int64_t> c(nb32);
+        SP_CUDA(cudaMemcpyAsync(c.data(), cost.p, nb32 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+        std::vector<int32_t> table;
+        for (int b = 1; b <= kMaxOcc; ++b) {
+            const int64_t W = (int64_t)kPartWarps * b * sms;
+            if (W % kSchedCtaWarps || (b * kPartWarps) % kSchedCtaWarps) continue;  // whole CTAs per SM only
+            const int64_t rounds = (nb32 + W - 1) / W;
+            P.sched_off[b] = (int64_t)table.size();
+            P.sched_rounds[b] = (int32_t)rounds;
+            table.resize(table.size() + rounds * W, -1);
+            int32_t *t = table.data() + P.sched_off[b];
+            std::vector<int64_t> load(W, 0);
+            int32_t blk[kSchedCtaWarps], wrp[kSchedCtaWarps];
+            for (int64_t r = 0; r < rounds; ++r) {
+                for (int64_t cta = 0; cta < W / kSchedCtaWarps; ++cta) {
+                    const int64_t first = r * W + cta * kSchedCtaWarps;
+                    int n = 0;
+                    for (int j = 0; j < kSchedCtaWarps && first + j < nb32; ++j) blk[n++] = (int32_t)(first + j);
+                    if (!n) continue;
+                    int64_t *ld = load.data() + cta * kSchedCtaWarps;
+                    for (int j = 0; j < kSchedCtaWarps; ++j) wrp[j] = j;
+                    std::stable_sort(blk, blk + n, [&](int32_t x, int32_t y) { return c[x] > c[y]; });
+                    std::stable_sort(wrp, wrp + kSchedCtaWarps, [&](int32_t x, int32_t y) { return ld[x] < ld[y]; });
+                    for (int i = 0; i < n; ++i) {
+                        t[r * W + cta * kSchedCtaWarps + wrp[i]] = blk[i];
+                        ld[wrp[i]] += c[blk[i]];
+                    }
+                }
+            }
+        }
+        if (!table.empty()) {
+            SP_TRY(dev_alloc(P.sched, table.size() * sizeof(int32_t), s));
+            SP_CUDA(cudaMemcpyAsync(P.sched->ptr, table.data(), table.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+            SP_CUDA(cudaStreamSynchronize(s));
+        }
+    }
     return SP_OK;
 }
 

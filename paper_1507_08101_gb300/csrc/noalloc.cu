@@ -124,6 +124,8 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     a.dot_off = 0;
     a.partials = na->partials;
     a.ticket = na->ticket;
+    a.sched = nullptr;
+    a.sched_rounds = 0;
     a.wbounds = nullptr;
     a.wbounds_src = nullptr;
     a.nsm = 0;

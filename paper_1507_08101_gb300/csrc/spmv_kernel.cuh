@@ -68,6 +68,8 @@ struct SpmvArgs {
     int32_t dot_stride, dot_off;
     double *partials;
     unsigned *ticket;
+    const int32_t *sched;    // moving-front schedule of this grid (null: see wbounds)
+    int32_t sched_rounds;
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
     int32_t nsm;             // SMs the grid was sized for
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
@@ -507,7 +509,22 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
     };
 
-    if (a.wbounds) {
+    if (a.sched) {
+        // moving front: in round r this warp takes one 32-slot block of the
+        // run of adjacent blocks the whole grid covers in that round
+        const int64_t W = (int64_t)gridDim.x * kMainWarps;
+        const int64_t me = (int64_t)blockIdx.x * kMainWarps + warp;
+        int kb = a.sched[me];
+        for (int r = 0; r < a.sched_rounds; ++r) {
+            const int knext = r + 1 < a.sched_rounds ? a.sched[(int64_t)(r + 1) * W + me] : -1;
+            if (kb >= 0) {
+                const int64_t s0 = (int64_t)kb * 32;
+                const int64_t s1 = s0 + 32 < a.nslots ? s0 + 32 : a.nslots;
+                for (int64_t s = s0 + rw; s < s1; s += Rr) slot(meta_of(s));
+            }
+            kb = knext;
+        }
+    } else if (a.wbounds) {
         // static cost-balanced partition: this warp owns a contiguous slot range
 #if SP_SWIZZLE
         const int nsm = a.nsm, per = gridDim.x / nsm;

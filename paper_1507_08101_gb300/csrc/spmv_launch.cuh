@@ -12,9 +12,11 @@
 namespace sp {
 
 // Row order of the product kernel: 0 = static cost-balanced contiguous range
-// per warp; 1 = block-strided front (all warps near the same rows).
+// per warp; 1 = block-strided front (all warps near the same rows);
+// 2 = moving front with a balanced assignment (falls back to 0 when the grid
+// has no schedule).
 #ifndef SP_ORDER
-#define SP_ORDER 0
+#define SP_ORDER 2
 #endif
 
 // Preferred shared-memory carveout (percent of the unified L1/shared array
@@ -48,11 +50,15 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     if (grid > max_blocks) grid = max_blocks;
     // with a partition table the whole persistent grid runs (idle warps exit at
     // once), so even a small matrix is spread over every SM
-    const bool part = SP_ORDER == 0 && a.wbounds_src && partition_for(*a.wbounds_src, grid * kMainWarps);
+    const bool part = SP_ORDER != 1 && a.wbounds_src && partition_for(*a.wbounds_src, grid * kMainWarps);
     if (!part && grid > need) grid = need;
     if (grid < 1) grid = 1;
     SpmvArgs b = a;
     b.wbounds = part ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
+    b.sched = nullptr;
+    b.sched_rounds = 0;
+    if (SP_ORDER == 2 && part && kMainWarps == kSchedCtaWarps)
+        b.sched = schedule_for(*a.wbounds_src, grid * kMainWarps, &b.sched_rounds);
     b.nsm = sms;
     b.log2_tpr = lt;
     k_spmmv<VT, XT, WP, VEC, DOTS, MT><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
