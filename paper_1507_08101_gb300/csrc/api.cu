@@ -33,6 +33,17 @@ int device_sm_count(int *n) {
     return SP_OK;
 }
 
+size_t device_l2_bytes() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev] && cudaDeviceGetAttribute(&cached[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (size_t)cached[dev];
+}
+
 // Scratch for the fused dot products: one partial per (value, block) for up to
 // 8 resident blocks per SM (2048 threads / 256) and 3 x 32 values, plus the
 // arrival ticket.

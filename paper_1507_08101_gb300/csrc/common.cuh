@@ -147,6 +147,7 @@ int launch_sampled(const Pattern &P, sp_dtype xdt, int w, const void *x, const v
                    cudaStream_t s);
 
 int device_sm_count(int *n);
+size_t device_l2_bytes();
 int build_partition(Pattern &P, cudaStream_t s);
 constexpr int kPartWarps = 8;  // warps per block of the partitioned kernels
 constexpr int kSchedCtaWarps = 32;  // warps per CTA the front schedule is built for

@@ -57,7 +57,11 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.wbounds = part ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
     b.sched = nullptr;
     b.sched_rounds = 0;
-    if (SP_ORDER == 2 && part && kMainWarps == kSchedCtaWarps)
+    // the moving front pays when x does not fit in L2 (its reuse across rows
+    // must then come from L2); otherwise the contiguous ranges keep more of
+    // x in L1
+    if (SP_ORDER == 2 && part && kMainWarps == kSchedCtaWarps &&
+        (double)a.wbounds_src->ncols * a.w * sizeof(XT) > 0.5 * (double)device_l2_bytes())
         b.sched = schedule_for(*a.wbounds_src, grid * kMainWarps, &b.sched_rounds);
     b.nsm = sms;
     b.log2_tpr = lt;
