@@ -432,8 +432,13 @@ def secondary_powerlaw(peak):
     import torch
     from paper_1507_08101_gb300 import sellcs
     from workloads import generators as gen
+    from paper_1507_08101_gb300 import autotune
     A, X, G = gen.workload_powerlaw()
-    m = sellcs.SellMatrix(A, C=32, sigma=256, dtype="f32", with_transpose=True)
+    t0 = time.perf_counter()
+    tuned = autotune.tune_spmv(A, 4, "f32", "f32", with_transpose=True, cache_path=None)
+    tune_s = time.perf_counter() - t0
+    m = sellcs.SellMatrix(A, C=tuned["C"], sigma=tuned["sigma"], dtype="f32", with_transpose=True,
+                          order=tuned["order"])
     inf = m.info()
     x = torch.from_numpy(X).to("cuda", torch.float32)
     g = torch.from_numpy(G).to("cuda", torch.float32)
@@ -446,10 +451,13 @@ def secondary_powerlaw(peak):
         sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv)
     fwd = _events_time(lambda: sellcs.spmv(m, x, y), 50, stream)
     bwd = _events_time(lambda: sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv), 50, stream)
-    nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * 32, 4, 4, 4, False, False, True)
+    C = tuned["C"]
+    nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * C, 4, 4, 4, False, False,
+                           tuned["sigma"] > 1)
     # backward: A^T product (same byte count) + sampled: col index + dvals write per nonzero, g and x once
-    nb_bwd = nb + A.nnz * (4 + 4) + 2 * A.nrows * 4 * 4 + inf["nchunks"] * 32 * 8
-    return {"nnz": A.nnz, "fwd_us": round(fwd * 1e3, 1), "fwd_GBs": round(nb / fwd / 1e6, 1),
+    nb_bwd = nb + A.nnz * (4 + 4) + 2 * A.nrows * 4 * 4 + inf["nchunks"] * C * 8
+    return {"nnz": A.nnz, "tuned": {k: tuned[k] for k in ("C", "sigma", "order")}, "autotune_s": round(tune_s, 2),
+            "nstored": inf["nstored"], "fwd_us": round(fwd * 1e3, 1), "fwd_GBs": round(nb / fwd / 1e6, 1),
             "bwd_us": round(bwd * 1e3, 1), "bwd_GBs": round(nb_bwd / bwd / 1e6, 1)}
 
 

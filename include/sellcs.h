@@ -76,6 +76,12 @@ typedef struct sp_dense sp_dense; /* opaque: dense block vector (owning or view)
 #define SP_MAT_CSR_ON_DEVICE (1u << 0)  /* rowptr, col, val are device pointers (else host) */
 #define SP_MAT_VAL_F32 (1u << 1)        /* val points to float (else double) */
 #define SP_MAT_WITH_TRANSPOSE (1u << 2) /* also build A^T in SELL-C-sigma (needed by sp_spmv_adjoint) */
+/* Work order of the product kernels over this matrix (and its transpose); at
+ * most one of the two.  Neither: chosen per call, the moving front when the
+ * block vector x is larger than half of L2, the contiguous ranges otherwise.
+ * The order changes only which warp computes which row, never a result. */
+#define SP_MAT_ORDER_FRONT (1u << 3)  /* moving front: all warps work on one run of rows at a time */
+#define SP_MAT_ORDER_RANGES (1u << 4) /* each warp owns one contiguous cost-balanced range of rows */
 
 /*
  * Build a SELL-C-sigma matrix from CSR (GHOST: "construct a SELL-C-sigma matrix

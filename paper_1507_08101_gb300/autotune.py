@@ -1,14 +1,17 @@
-"""Autotuner of the batched SpMMV launch configuration.
+"""Autotuner of the SpMMV launch configuration.
 
-It picks the SELL chunk height C, the sort window sigma and the lane layout
-(columns per lane CPL, hence G = WP / CPL lanes per column group and, through C,
-the threads per row T) by timing candidates on the GPU with CUDA events:
-either jointly for a whole batch (:func:`tune_batch_joint`: every candidate
-batch is built with sp_mat_create_csr and multiplied by one sp_batch launch,
-the kernel the solver runs) or per matrix (:func:`tune_batch`: each matrix
-through a one-matrix sp_batch).  Results are cached in a JSON
-file under a structural signature of the matrix (size, nonzeros, row-length
-histogram) and the block width, so equal structures are tuned once.
+For the batched kernel it picks the SELL chunk height C, the sort window sigma
+and the lane layout (columns per lane CPL, hence G = WP / CPL lanes per column
+group and, through C, the threads per row T) by timing candidates on the GPU
+with CUDA events: either jointly for a whole batch (:func:`tune_batch_joint`:
+every candidate batch is built with sp_mat_create_csr and multiplied by one
+sp_batch launch, the kernel the solver runs) or per matrix (:func:`tune_batch`:
+each matrix through a one-matrix sp_batch).  For a single matrix multiplied by
+sp_spmv (and differentiated by sp_spmv_adjoint) :func:`tune_spmv` picks C,
+sigma and the work order (moving front or contiguous ranges).  Results are
+cached in a JSON file under a structural signature of the matrix (size,
+nonzeros, row-length histogram) and the block width, so equal structures are
+tuned once.
 
 This module only orchestrates calls into the CUDA library; the timed work is
 the library's kernels.
@@ -174,3 +177,58 @@ def tune_batch(mats, widths, dtype: str = "f32", vec_dtype: str = "f32", cache_p
     if dirty:
         _store_cache(cache_path, cache)
     return out
+
+
+SPMV_C_CANDIDATES = (4, 8, 16, 32)
+SPMV_ORDERS = ("front", "ranges")
+
+
+def tune_spmv(A, w: int, dtype: str = "f64", vec_dtype: str = "f64", with_transpose: bool = False,
+              cache_path: str | None = DEFAULT_CACHE, reps: int = 20, Cs=SPMV_C_CANDIDATES, sigmas=None,
+              orders=SPMV_ORDERS) -> dict:
+    """{C, sigma, order, us} for y = A x through sp_spmv at block width w (and,
+    with ``with_transpose``, the adjoint sp_spmv_adjoint as well: the objective
+    is then the forward plus the backward time).  sigma candidates default to
+    1, 256 and the whole matrix."""
+    import torch
+    key = f"spmv:{signature(A, w, dtype)}:{vec_dtype}:{int(with_transpose)}"
+    cache = _load_cache(cache_path)
+    if key not in cache:
+        if sigmas is None:
+            sigmas = tuple(sorted({1, 256, max(1, int(A.nrows))}))
+        tdt = torch.float32 if vec_dtype == "f32" else torch.float64
+        x = torch.rand(A.ncols, w, dtype=tdt, device="cuda")
+        y = torch.empty(A.nrows, w, dtype=tdt, device="cuda")
+        g = torch.rand(A.nrows, w, dtype=tdt, device="cuda") if with_transpose else None
+        dx = torch.empty_like(x) if with_transpose else None
+        dv = torch.empty(A.nnz, dtype=tdt, device="cuda") if with_transpose else None
+        best = None
+        for C in Cs:
+            for sigma in sigmas:
+                if 1 < sigma < C:
+                    continue
+                for order in orders:
+                    m = sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=dtype, with_transpose=with_transpose,
+                                          order=order)
+
+                    def step():
+                        sellcs.spmv(m, x, y)
+                        if with_transpose:
+                            sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv)
+
+                    for _ in range(3):
+                        step()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        step()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    us = e0.elapsed_time(e1) * 1e3 / reps
+                    m.close()
+                    if best is None or us < best["us"]:
+                        best = {"C": C, "sigma": int(sigma), "order": order, "us": round(us, 2)}
+        cache[key] = best
+        _store_cache(cache_path, cache)
+    return dict(cache[key])

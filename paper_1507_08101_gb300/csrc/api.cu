@@ -71,11 +71,12 @@ static int max_blocks_of(const sp_mat *A) {
 }
 
 int launch_spmv(const SpmvLaunch &L, cudaStream_t s) {
-    SpmvArgs a;
+    SpmvArgs a{};
     const Pattern &P = *L.P;
     a.val = L.val;
     a.col = (const int32_t *)P.col->ptr;
     a.chunkptr = (const int64_t *)P.chunkptr->ptr;
+    a.chunklen = (const int32_t *)P.chunklen->ptr;
     a.slotlen = (const int32_t *)P.slotlen->ptr;
     a.perm = P.sigma == 1 ? nullptr : (const int32_t *)P.perm->ptr;
     a.nrows = P.nrows;
@@ -197,7 +198,10 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     if (nrows < 0 || ncols < 0 || nrows >= (1LL << 31) || ncols >= (1LL << 31)) return SP_ERR_DIM;
     if (C < 1 || C > 1024 || sigma < 1) return SP_ERR_ARG;
     if (!valid_val_dtype(val_dtype)) return SP_ERR_DTYPE;
-    if (flags & ~(SP_MAT_CSR_ON_DEVICE | SP_MAT_VAL_F32 | SP_MAT_WITH_TRANSPOSE)) return SP_ERR_ARG;
+    if (flags & ~(SP_MAT_CSR_ON_DEVICE | SP_MAT_VAL_F32 | SP_MAT_WITH_TRANSPOSE | SP_MAT_ORDER_FRONT |
+                  SP_MAT_ORDER_RANGES))
+        return SP_ERR_ARG;
+    if ((flags & SP_MAT_ORDER_FRONT) && (flags & SP_MAT_ORDER_RANGES)) return SP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     bool on_dev = flags & SP_MAT_CSR_ON_DEVICE;
     bool f32 = flags & SP_MAT_VAL_F32;
@@ -232,6 +236,11 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     A->vdt = val_dtype;
     int rc = build_pattern_and_values(A, nrows, ncols, prp, pcol, pval, f32, C, sigma, s);
     if (rc == SP_OK && (flags & SP_MAT_WITH_TRANSPOSE)) rc = build_transpose(A, prp, pcol, pval, f32, s);
+    if (rc == SP_OK) {
+        const int order = (flags & SP_MAT_ORDER_FRONT) ? 1 : (flags & SP_MAT_ORDER_RANGES) ? 2 : 0;
+        A->pat->order = order;
+        if (A->transpose) A->transpose->pat->order = order;
+    }
     if (rc == SP_OK) rc = ensure_scratch(A, s);
     if (rc == SP_OK && A->transpose) rc = ensure_scratch(A->transpose, s);
     if (rc == SP_OK) {

@@ -100,12 +100,6 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
         const int64_t off = M.chunkptr[cidx] + ((uint32_t)s - cidx * (uint32_t)M.C) + (int64_t)tt * M.C;
         const int len = M.slotlen[s];
         const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
-        // the epilogue's loads go out before the row loop
-        XT xi[CPL], yo[CPL], t[CPL];
-        if (tt == 0 && nvalid > 0) {
-            if (need_xi) load_cols<XT, CPL, true>(xk + i * M.w, 1, nvalid, xi);
-            if (f & SP_SPMV_AXPBY) load_out<XT, CPL, true>((const XT *)M.y0 + i * M.w + k0, 1, nvalid, yo);
-        }
         AT acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
@@ -117,6 +111,9 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
             if (tt != 0) continue;
         }
         if (nvalid <= 0) continue;
+        XT xi[CPL], yo[CPL], t[CPL];
+        if (need_xi) load_cols<XT, CPL, true>(xk + i * M.w, 1, nvalid, xi);
+        if (f & SP_SPMV_AXPBY) load_out<XT, CPL, true>((const XT *)M.y0 + i * M.w + k0, 1, nvalid, yo);
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             XT v = (XT)acc[c];

@@ -70,6 +70,10 @@ struct Pattern {
     DevBufPtr sched;     // int32
     int64_t sched_off[9] = {0};
     int32_t sched_rounds[9] = {0};
+    // spread of the row lengths inside 32-slot blocks: sum over blocks of
+    // (longest - shortest real row) / sum of the longest
+    double lane_spread = 0.0;
+    int order = 0;  // work order of the product: 0 by the size of x, 1 moving front, 2 contiguous ranges
 };
 using PatternPtr = std::shared_ptr<Pattern>;
 

@@ -13,6 +13,7 @@
 // The transpose (for the adjoint) is built the same way from the CSR of A^T,
 // which comes from a stable ascending merge sort of the entries by column.
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "common.cuh"
@@ -373,6 +374,39 @@ __global__ void k_block32_cost(const int32_t *__restrict__ slotlen, int64_t nslo
     }
 }
 
+// per 32-slot block: longest and shortest real row; out[0] += longest -
+// shortest, out[1] += longest (one atomic per warp)
+__global__ void k_block_spread(const int32_t *__restrict__ slotlen, int64_t nslots, int64_t nrows, int64_t nb32,
+                               unsigned long long *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t kend = (nb32 + 31) / 32 * 32;  // whole warps run every iteration
+    for (int64_t k = k0; k < kend; k += stride) {
+        unsigned long long d = 0, m = 0;
+        if (k < nb32) {
+            int lo = INT_MAX, hi = 0;
+            const int64_t e = min(32 * k + 32, min(nslots, nrows));
+            for (int64_t s = 32 * k; s < e; ++s) {
+                lo = min(lo, slotlen[s]);
+                hi = max(hi, slotlen[s]);
+            }
+            if (hi > 0) {
+                d = (unsigned long long)(hi - lo);
+                m = (unsigned long long)hi;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+            m += __shfl_xor_sync(0xffffffffu, m, o);
+        }
+        if ((threadIdx.x & 31) == 0 && m > 0) {
+            atomicAdd(out, d);
+            atomicAdd(out + 1, m);
+        }
+    }
+}
+
 // bounds[t] = first block whose prefix cost reaches t/T of the total
 __global__ void k_partition(const int64_t *__restrict__ prefix, int64_t nb32, int64_t T,
                             int32_t *__restrict__ bounds) {
@@ -412,6 +446,18 @@ int build_partition(Pattern &P, cudaStream_t s) {
         SP_CUDA(cudaGetLastError());
     }
     SP_TRY(scan_exclusive(cost.as<int64_t>(), prefix.as<int64_t>(), nb32 + 1, s));
+    if (nb32 > 0) {
+        Tmp spread(s);
+        SP_TRY(spread.alloc(2 * sizeof(unsigned long long)));
+        SP_CUDA(cudaMemsetAsync(spread.p, 0, 2 * sizeof(unsigned long long), s));
+        k_block_spread<<<grid_for(nb32), kThreads, 0, s>>>((const int32_t *)P.slotlen->ptr, P.nslots, P.nrows, nb32,
+                                                            (unsigned long long *)spread.p);
+        SP_CUDA(cudaGetLastError());
+        unsigned long long h[2] = {0, 0};
+        SP_CUDA(cudaMemcpyAsync(h, spread.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+        P.lane_spread = h[1] ? (double)h[0] / (double)h[1] : 0.0;
+    }
     int64_t total = 0;
     for (int b = 1; b <= kMaxOcc; ++b) {
         P.bounds_off[b] = total;
@@ -441,11 +487,28 @@ int build_partition(Pattern &P, cudaStream_t s) {
             P.sched_rounds[b] = (int32_t)rounds;
             table.resize(table.size() + rounds * W, -1);
             int32_t *t = table.data() + P.sched_off[b];
-            std::vector<int64_t> load(W, 0);
+            // each round covers W adjacent blocks in runs of kSchedCtaWarps;
+            // the runs go to CTAs longest first, each to the CTA with the least
+            // work so far (so sorted rows do not load the low CTAs every round),
+            // and inside a CTA the blocks go to warps the same way
+            const int64_t nct = W / kSchedCtaWarps;
+            std::vector<int64_t> load(W, 0), cload(nct, 0), rcost(nct);
+            std::vector<int32_t> run(nct), ctas(nct);
             int32_t blk[kSchedCtaWarps], wrp[kSchedCtaWarps];
             for (int64_t r = 0; r < rounds; ++r) {
-                for (int64_t cta = 0; cta < W / kSchedCtaWarps; ++cta) {
-                    const int64_t first = r * W + cta * kSchedCtaWarps;
+                for (int64_t g = 0; g < nct; ++g) {
+                    run[g] = (int32_t)g;
+                    ctas[g] = (int32_t)g;
+                    rcost[g] = 0;
+                    for (int64_t j = r * W + g * kSchedCtaWarps; j < r * W + (g + 1) * kSchedCtaWarps && j < nb32; ++j)
+                        rcost[g] += c[j];
+                }
+                std::stable_sort(run.begin(), run.end(), [&](int32_t x, int32_t y) { return rcost[x] > rcost[y]; });
+                std::stable_sort(ctas.begin(), ctas.end(), [&](int32_t x, int32_t y) { return cload[x] < cload[y]; });
+                for (int64_t q = 0; q < nct; ++q) {
+                    const int64_t cta = ctas[q];
+                    const int64_t first = r * W + (int64_t)run[q] * kSchedCtaWarps;
+                    cload[cta] += rcost[run[q]];
                     int n = 0;
                     for (int j = 0; j < kSchedCtaWarps && first + j < nb32; ++j) blk[n++] = (int32_t)(first + j);
                     if (!n) continue;

@@ -95,10 +95,11 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     SP_CUDA(cudaMemsetAsync(na->ticket, 0, sizeof(unsigned), s));
 
     const int64_t nchunks = (nrows + C - 1) / C;
-    SpmvArgs a;
+    SpmvArgs a{};
     a.val = val;
     a.col = col;
     a.chunkptr = chunkptr;
+    a.chunklen = nullptr;  // chunk lengths are not among this entry point's arguments
     a.slotlen = slotlen;
     a.perm = perm;
     a.nrows = nrows;

@@ -50,6 +50,7 @@ struct SpmvArgs {
     const void *val;
     const int32_t *col;
     const int64_t *chunkptr;
+    const int32_t *chunklen;  // null: the row loop runs per lane (see row_product_ls)
     const int32_t *slotlen;
     const int32_t *perm;  // null: identity (sigma = 1)
     int64_t nrows;
@@ -261,6 +262,78 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
     }
 }
 
+// Lockstep form of row_product: every lane of a chunk steps through the
+// chunk's length clen (the same for all of them), and the entries past a lane's
+// own row length are predicated off.  The warp then issues one step per column
+// of the chunk instead of running the lanes' different tails one after the
+// other (on the float64 pipe a step costs the same whatever lanes are active).
+// The products are added in the order j = 0, 1, ..., len - 1, as in
+// row_product, so the two give identical sums.
+// SP_LOCKSTEP: 0 never, 1 where it pays (float64 products: always for block
+// vectors, for single vectors when the row lengths inside a warp's slots
+// spread widely), 2 always.
+#ifndef SP_LOCKSTEP
+#define SP_LOCKSTEP 1
+#endif
+#ifndef SP_LS_SPREAD
+#define SP_LS_SPREAD 0.3
+#endif
+#ifndef SP_LS_SPREAD_DOTS
+#define SP_LS_SPREAD_DOTS 0.15
+#endif
+template <class VT, class XT, class AT, int CPL, bool VEC, int U>
+__device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
+                                               int len, int clen, const XT *__restrict__ xk, int64_t xrs,
+                                               int64_t xcs, int nvalid, AT (&acc)[CPL]) {
+    int j = 0;
+    for (; j + U <= clen; j += U) {
+        int32_t cc[U];
+        VT vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = j + u < len;
+            cc[u] = ok ? ld_stream(cp + (int64_t)u * C) : 0;
+            vv[u] = ok ? ld_stream(vp + (int64_t)u * C) : VT(0);
+        }
+        vp += (int64_t)U * C;
+        cp += (int64_t)U * C;
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j + u < len) {
+                    XT xv[CPL];
+                    load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+                    AT v = val_to_acc<AT, VT>(vv[u]);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                }
+            }
+        }
+    }
+    const int rest = len - j;
+    if (clen > j) {
+        int32_t cc[U];
+        VT vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
+            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : VT(0);
+        }
+        if (nvalid > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u < rest) {
+                    XT xv[CPL];
+                    load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
+                    AT v = val_to_acc<AT, VT>(vv[u]);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                }
+            }
+        }
+    }
+}
+
 // Row sums t[c] = sum_j val(s,j) * x[col(s,j), k0 + c] for the row in one slot.
 // U value/index loads and U gathers are in flight per step; the last
 // (len mod U) entries are issued the same way under a predicate, so a short
@@ -390,7 +463,7 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool LS>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
@@ -432,7 +505,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     // the offset of its first entry and its length.  Three independent loads.
     struct Meta {
         int64_t i, off;
-        int len;
+        int len, clen;
     };
     auto meta_of = [&](int64_t s) {
         Meta m;
@@ -440,6 +513,8 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         const uint32_t cidx = (uint32_t)s / (uint32_t)a.C;
         m.off = a.chunkptr[cidx] + (int64_t)((uint32_t)s - cidx * (uint32_t)a.C);
         m.len = a.slotlen[s];
+        // without chunk lengths each lane runs to its own length (same sums)
+        m.clen = (LS && a.chunklen) ? a.chunklen[cidx] : m.len;
         return m;
     };
 
@@ -462,8 +537,13 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             AT acc[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-            row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                                 a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
+            if constexpr (LS)
+                row_product_ls<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
+                                                        a.C << lt, len_t, (m.clen + T - 1) >> lt, xk, a.xrs, a.xcs,
+                                                        nvalid, acc);
+            else
+                row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
+                                                     a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
             if (MT && T > 1) {
                 // combine the T partial sums of the row (fixed xor tree)
 #pragma unroll
@@ -539,10 +619,10 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         int64_t s = s0 + rw;
         if (SP_PREFETCH_META) {
             // the next slot's metadata is loaded while this slot is computed
-            Meta cur{-1, 0, 0};
+            Meta cur{-1, 0, 0, -1};
             if (s < s1) cur = meta_of(s);
             for (; s < s1; s += Rr) {
-                Meta nxt{-1, 0, 0};
+                Meta nxt{-1, 0, 0, -1};
                 if (s + Rr < s1) nxt = meta_of(s + Rr);
                 slot(cur);
                 cur = nxt;

@@ -7,6 +7,8 @@
 // fallback chain); wider blocks are processed in tiles of 32 columns.
 #pragma once
 
+#include <type_traits>
+
 #include "spmv_kernel.cuh"
 
 namespace sp {
@@ -19,13 +21,18 @@ namespace sp {
 #define SP_ORDER 2
 #endif
 
+// The moving front is taken when x is larger than this fraction of L2.
+#ifndef SP_FRONT_X_L2_FRAC
+#define SP_FRONT_X_L2_FRAC 0.5
+#endif
+
 // Preferred shared-memory carveout (percent of the unified L1/shared array
 // given to shared memory); negative: leave the driver's choice.
 #ifndef SP_CARVEOUT
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT>
+template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool LS>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
@@ -33,9 +40,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS>,
                                                                       kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -57,27 +64,51 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.wbounds = part ? partition_for(*a.wbounds_src, grid * kMainWarps) : nullptr;
     b.sched = nullptr;
     b.sched_rounds = 0;
-    // the moving front pays when x does not fit in L2 (its reuse across rows
-    // must then come from L2); otherwise the contiguous ranges keep more of
-    // x in L1
-    if (SP_ORDER == 2 && part && kMainWarps == kSchedCtaWarps &&
-        (double)a.wbounds_src->ncols * a.w * sizeof(XT) > 0.5 * (double)device_l2_bytes())
-        b.sched = schedule_for(*a.wbounds_src, grid * kMainWarps, &b.sched_rounds);
+    // unless the matrix names an order: the moving front pays when x does not
+    // fit in L2 (its reuse across rows must then come from L2); otherwise the
+    // contiguous ranges keep more of x in L1
+    if (SP_ORDER == 2 && part && kMainWarps == kSchedCtaWarps) {
+        const int order = a.wbounds_src->order;
+        const bool front = order == 1 || (order == 0 && (double)a.wbounds_src->ncols * a.w * sizeof(XT) >
+                                                            SP_FRONT_X_L2_FRAC * (double)device_l2_bytes());
+        if (front) b.sched = schedule_for(*a.wbounds_src, grid * kMainWarps, &b.sched_rounds);
+    }
     b.nsm = sms;
     b.log2_tpr = lt;
-    k_spmmv<VT, XT, WP, VEC, DOTS, MT><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
+    k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
-template <class VT, class XT, int WP, bool MT>
-static int launch_spmv_wm(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+template <class VT, class XT, int WP, bool MT, bool LS>
+static int launch_spmv_wml(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     const bool dots = (a.flags & SP_SPMV_DOT_ANY) != 0;
     if (dots)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, true, MT>(a, max_blocks, s);
-    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false, false, MT>(a, max_blocks, s);
+        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT, LS>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, true, MT, LS>(a, max_blocks, s);
+    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT, LS>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, false, MT, LS>(a, max_blocks, s);
+}
+
+// Lockstep row loop (row_product_ls) or per-lane loop: the lockstep form saves
+// float64-pipe steps when lanes of a warp have rows of different lengths, and
+// costs a few instructions per step; it is used only where the float64 pipe
+// binds (float64 values and vectors).
+template <class VT, class XT, int WP, bool MT>
+static int launch_spmv_wm(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+    constexpr bool f64 = std::is_same<VT, double>::value && std::is_same<XT, double>::value;
+    if constexpr (!f64 || SP_LOCKSTEP == 0) {
+        return launch_spmv_wml<VT, XT, WP, MT, false>(a, vec, max_blocks, s);
+    } else if constexpr (WP >= 2 || SP_LOCKSTEP == 2) {
+        return launch_spmv_wml<VT, XT, WP, MT, true>(a, vec, max_blocks, s);
+    } else {
+        // the fused dots and the chain add float64 work per row, so the pipe
+        // binds already at a smaller spread
+        const double thr = (a.flags & (SP_SPMV_DOT_ANY | SP_SPMV_CHAIN_AXPBY)) ? SP_LS_SPREAD_DOTS : SP_LS_SPREAD;
+        const bool ls = a.wbounds_src && a.wbounds_src->lane_spread > thr;
+        return ls ? launch_spmv_wml<VT, XT, WP, MT, true>(a, vec, max_blocks, s)
+                  : launch_spmv_wml<VT, XT, WP, MT, false>(a, vec, max_blocks, s);
+    }
 }
 
 template <class VT, class XT, int WP>

@@ -23,6 +23,8 @@ SP_ERR_ARG, SP_ERR_DIM, SP_ERR_DTYPE, SP_ERR_CUDA, SP_ERR_OOM, SP_ERR_TIMEOUT, S
 SP_F64, SP_F32, SP_BF16 = 0, 1, 2
 SP_ROW_MAJOR, SP_COL_MAJOR = 0, 1
 SP_MAT_CSR_ON_DEVICE, SP_MAT_VAL_F32, SP_MAT_WITH_TRANSPOSE = 1, 2, 4
+SP_MAT_ORDER_FRONT, SP_MAT_ORDER_RANGES = 8, 16
+ORDERS = {"auto": 0, "front": SP_MAT_ORDER_FRONT, "ranges": SP_MAT_ORDER_RANGES}
 SP_SPMV_SCALE = 1 << 0
 SP_SPMV_SHIFT = 1 << 1
 SP_SPMV_VSHIFT = 1 << 2
@@ -217,10 +219,10 @@ class SellMatrix:
     a tuple (nrows, ncols, rowptr, col, val) of CUDA tensors (then the CSR is
     read on the device)."""
 
-    def __init__(self, csr, C=32, sigma=1, dtype="f64", with_transpose=False, stream=None):
+    def __init__(self, csr, C=32, sigma=1, dtype="f64", with_transpose=False, stream=None, order="auto"):
         import torch
         self._lib = lib()
-        flags = SP_MAT_WITH_TRANSPOSE if with_transpose else 0
+        flags = (SP_MAT_WITH_TRANSPOSE if with_transpose else 0) | ORDERS[order]
         if isinstance(csr, tuple):
             nrows, ncols, rowptr, col, val = csr
             flags |= SP_MAT_CSR_ON_DEVICE

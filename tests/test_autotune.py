@@ -68,3 +68,40 @@ def test_joint_tuning(cuda_ok, tmp_path):
         assert w % c["cpl"] == 0 and c["cpl"] <= 4
     assert autotune.tune_batch_joint(mats, widths, cache_path=str(tmp_path / "j.json"), reps=5,
                                      Cs=(16, 32), sigmas=(1, 32)) == cfg
+
+
+@pytest.mark.gpu
+def test_tune_spmv_forward_and_adjoint(cuda_ok, tmp_path):
+    """The single-matrix tuner returns a candidate configuration, caches it, and
+    the matrix built with it gives the oracle's product and adjoint."""
+    import torch
+    import oracle
+    from paper_1507_08101_gb300 import sellcs
+    from tests.gpu_helpers import to_dev
+    A = gen.powerlaw(20000, seed=17)
+    cache = str(tmp_path / "tune.json")
+    cfg = autotune.tune_spmv(A, 4, "f32", "f32", with_transpose=True, cache_path=cache, reps=3, Cs=(8, 32))
+    assert cfg["C"] in (8, 32) and cfg["sigma"] in (1, 256, A.nrows) and cfg["order"] in autotune.SPMV_ORDERS
+    assert autotune.tune_spmv(A, 4, "f32", "f32", with_transpose=True, cache_path=cache, reps=3,
+                              Cs=(8, 32)) == cfg
+    m = sellcs.SellMatrix(A, C=cfg["C"], sigma=cfg["sigma"], dtype="f32", with_transpose=True, order=cfg["order"])
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (A.ncols, 4)).astype(np.float32).astype(np.float64)
+    G = rng.uniform(-1, 1, (A.nrows, 4)).astype(np.float32).astype(np.float64)
+    x, g = to_dev(X, torch.float32), to_dev(G, torch.float32)
+    y = torch.empty_like(x)
+    sellcs.spmv(m, x, y)
+    dx, dv = torch.empty_like(x), torch.empty(A.nnz, dtype=torch.float32, device="cuda")
+    sellcs.spmv_adjoint(m, g, x=x, dx=dx, dvals=dv)
+    torch.cuda.synchronize()
+    vals = oracle.round_values(A.val, "f32")
+    yr, _, _ = oracle.spmmv(A, X, val=vals)
+    dxr = oracle.spmmv_transpose(A, G, val=vals)
+    dvr = oracle.sampled_product(A, G, X)
+    maxlen = int(np.diff(A.rowptr).max())
+    tol = 1.1 * (maxlen + 6) * 2.0 ** -24
+    s = oracle.spmmv_scale(A, X, val=vals)
+    assert np.all(np.abs(y.double().cpu().numpy() - yr) <= tol * (s + np.abs(yr)) + 1e-30)
+    sT = np.abs(oracle.spmmv_transpose(A, np.abs(G), val=np.abs(vals)))
+    assert np.all(np.abs(dx.double().cpu().numpy() - dxr) <= 2 * tol * (sT + np.abs(dxr)) + 1e-30)
+    np.testing.assert_allclose(dv.double().cpu().numpy(), dvr, rtol=tol * 8, atol=tol * 8)

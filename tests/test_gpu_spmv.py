@@ -182,6 +182,31 @@ def test_threads_per_row_long_rows(cuda_ok, C):
         run_case(A, C, 64, 4, ALL, vdt=vdt, xdt=xdt)
 
 
+@pytest.fixture(scope="module")
+def irregular_large():
+    """About 400k rows (more 32-row blocks than warps in one grid, so the moving
+    front takes several rounds), empty rows included."""
+    return gen.irregular_band(400_003, lmin=0, lmax=24, band=2000, seed=31)
+
+
+@pytest.mark.parametrize("vdt,xdt", [("f64", "f64"), ("f32", "f32")])
+@pytest.mark.parametrize("C,sigma", [(32, 1), (32, 256), (8, 1 << 20)])
+@pytest.mark.parametrize("w", [1, 16])
+def test_work_order_does_not_change_results(cuda_ok, irregular_large, vdt, xdt, C, sigma, w):
+    """Moving front, contiguous ranges and the automatic choice (and with them
+    the lockstep or per-lane row loop, chosen by the row-length spread) give
+    bit-identical y; each matches the oracle."""
+    A = irregular_large
+    ys = []
+    for order in ("auto", "front", "ranges"):
+        m = sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=vdt, order=order)
+        y, _, _ = run_case(A, C, sigma, w, {"scale", "shift", "axpby", "dot_yy", "dot_xy", "chain"}, vdt=vdt,
+                           xdt=xdt, mat=m, seed=7)
+        m.close()
+        ys.append(y)
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+
+
 def test_float64_extreme_magnitudes(cuda_ok):
     """x entries and matrix values of extreme magnitude (1e60, 3e-30, 1e45
     scaling), exact zeros and an infinity: the float64 tolerance holds and a
