@@ -68,15 +68,37 @@ struct BatchArgs {
     uint32_t flags;
     double alpha, beta;
     double *partials;  // [unit][3][kBatchMaxW]
+    unsigned *next;    // unit counter of the dynamic assignment (zero at launch)
 };
 
-template <class VT, class XT, int WP, int CPL>
-__device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, const BUnit &u, int lane,
+// Units go to warps dynamically (each warp takes the next unit from a counter)
+// when SP_BATCH_DYNAMIC is set, else statically (unit u to warp u mod warps).
+// Either way a unit's partial sums land in the unit's own slot and are added
+// in unit order, so the results do not depend on the assignment.
+#ifndef SP_BATCH_DYNAMIC
+#define SP_BATCH_DYNAMIC 1
+#endif
+// units per resident warp the work list is cut into
+#ifndef SP_BATCH_UNITS_PER_WARP
+#define SP_BATCH_UNITS_PER_WARP 8
+#endif
+
+// unroll depth of the row loop for 4-column lanes (knob)
+#ifndef SP_BATCH_UNROLL_WIDE
+#define SP_BATCH_UNROLL_WIDE SP_UNROLL_WIDE
+#endif
+
+// DM: the dot products this kernel accumulates (bit 0 <y,y>, bit 1 <x,y>,
+// bit 2 <x,x>), a compile-time set so that only their accumulators hold
+// registers; the flags pick which of them are written.
+template <class VT, class XT, int WP, int CPL, int DM>
+__device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__restrict__ Mp, const BUnit &u, int lane,
                                            double *part) {
     using AT = typename AccOf<VT, XT>::T;
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
+    constexpr int U = CPL >= 4 ? SP_BATCH_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
+    constexpr bool dots = DM != 0;
     const int lt = u.log2_tpr;
     const int T = 1 << lt;
     const int gl = lane % G;
@@ -84,72 +106,98 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat &M, co
     const int rw = (lane / G) >> lt;
     const int Rr = R >> lt;
     const unsigned rowmask = (G * T == 32) ? 0xffffffffu : (((1u << (G * T)) - 1u) << (rw * G * T));
+    const int w = Mp->w;
     const int k0 = gl * CPL;
-    const int nvalid = M.w - k0 < CPL ? M.w - k0 : CPL;
+    const int nvalid = w - k0 < CPL ? w - k0 : CPL;
     const uint32_t f = a.flags;
-    const bool dots = (f & SP_SPMV_DOT_ANY) != 0;
-    const bool need_xi = (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX)) != 0;
-    const VT *__restrict__ val = (const VT *)M.val;
-    const XT *__restrict__ xk = (const XT *)M.x + k0;
+    const bool need_xi = (DM & 6) != 0;
+    const VT *__restrict__ val = (const VT *)Mp->val;
+    const int32_t *__restrict__ colp = Mp->col;
+    const int64_t *__restrict__ chunkptr = Mp->chunkptr;
+    const int32_t *__restrict__ slotlen = Mp->slotlen;
+    const int32_t *__restrict__ perm = Mp->perm;
+    const int64_t nrows = Mp->nrows;
+    const uint32_t C = (uint32_t)Mp->C;
+    const XT *__restrict__ xk = (const XT *)Mp->x + k0;
     const XT alpha = (XT)a.alpha, beta = (XT)a.beta;
-    DotAcc<XT> ayy[CPL], axy[CPL], axx[CPL];
-    for (int64_t s = u.s0 + rw; s < u.s1; s += Rr) {
-        const int64_t i = M.perm ? (int64_t)M.perm[s] : (s < M.nrows ? s : -1);
-        if (i < 0) continue;
-        const uint32_t cidx = (uint32_t)s / (uint32_t)M.C;
-        const int64_t off = M.chunkptr[cidx] + ((uint32_t)s - cidx * (uint32_t)M.C) + (int64_t)tt * M.C;
-        const int len = M.slotlen[s];
-        const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
-        AT acc[CPL];
+    DotAcc<XT> ayy[(DM & 1) ? CPL : 1], axy[(DM & 2) ? CPL : 1], axx[(DM & 4) ? CPL : 1];
+    // where a slot's row lives; the next slot's is loaded while this one runs
+    struct Meta {
+        int64_t i, off;
+        int len;
+    };
+    auto meta_of = [&](int64_t s) {
+        Meta m;
+        m.i = perm ? (int64_t)perm[s] : (s < nrows ? s : -1);
+        const uint32_t cidx = (uint32_t)s / C;
+        m.off = chunkptr[cidx] + ((uint32_t)s - cidx * C) + (int64_t)tt * C;
+        m.len = slotlen[s];
+        return m;
+    };
+    int64_t s = u.s0 + rw;
+    Meta cur{-1, 0, 0};
+    if (s < u.s1) cur = meta_of(s);
+    for (; s < u.s1; s += Rr) {
+        Meta nxt{-1, 0, 0};
+        if (s + Rr < u.s1) nxt = meta_of(s + Rr);
+        const int64_t i = cur.i;
+        if (i >= 0) {
+            const int len_t = cur.len > tt ? (cur.len - tt + T - 1) >> lt : 0;
+            AT acc[CPL];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-        row_product<VT, XT, AT, CPL, true, U>(val + off, M.col + off, M.C << lt, len_t, xk, M.w, 1, nvalid, acc);
-        if (T > 1) {
+            for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+            row_product<VT, XT, AT, CPL, true, U>(val + cur.off, colp + cur.off, (int)C << lt, len_t, xk, w, 1,
+                                                  nvalid, acc);
+            bool epi = true;
+            if (T > 1) {
 #pragma unroll
-            for (int c = 0; c < CPL; ++c)
-                for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
-            if (tt != 0) continue;
-        }
-        if (nvalid <= 0) continue;
-        XT xi[CPL], yo[CPL], t[CPL];
-        if (need_xi) load_cols<XT, CPL, true>(xk + i * M.w, 1, nvalid, xi);
-        if (f & SP_SPMV_AXPBY) load_out<XT, CPL, true>((const XT *)M.y0 + i * M.w + k0, 1, nvalid, yo);
+                for (int c = 0; c < CPL; ++c)
+                    for (int o = G; o < G * T; o <<= 1) acc[c] += __shfl_xor_sync(rowmask, acc[c], o);
+                epi = tt == 0;
+            }
+            if (epi && nvalid > 0) {
+                XT xi[CPL], yo[CPL], t[CPL];
+                if (need_xi) load_cols<XT, CPL, true>(xk + i * w, 1, nvalid, xi);
+                if (f & SP_SPMV_AXPBY) load_out<XT, CPL, true>((const XT *)Mp->y0 + i * w + k0, 1, nvalid, yo);
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            XT v = (XT)acc[c];
-            if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
-            if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
-            t[c] = v;
-        }
-        store_out<XT, CPL, true>((XT *)M.y + i * M.w + k0, 1, nvalid, t);
-        if (dots) {
+                for (int c = 0; c < CPL; ++c) {
+                    XT v = (XT)acc[c];
+                    if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
+                    if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
+                    t[c] = v;
+                }
+                store_out<XT, CPL, true>((XT *)Mp->y + i * w + k0, 1, nvalid, t);
+                if constexpr (dots) {
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-                if (f & SP_SPMV_DOT_YY) ayy[c].add(t[c], t[c]);
-                if (f & SP_SPMV_DOT_XY) axy[c].add(xi[c], t[c]);
-                if (f & SP_SPMV_DOT_XX) axx[c].add(xi[c], xi[c]);
+                    for (int c = 0; c < CPL; ++c) {
+                        if constexpr ((DM & 1) != 0) ayy[c].add(t[c], t[c]);
+                        if constexpr ((DM & 2) != 0) axy[c].add(xi[c], t[c]);
+                        if constexpr ((DM & 4) != 0) axx[c].add(xi[c], xi[c]);
+                    }
+                }
             }
         }
+        cur = nxt;
     }
-    if (!dots) return;
+    if constexpr (!dots) return;
     double dyy[CPL], dxy[CPL], dxx[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-        dyy[c] = ayy[c].value();
-        dxy[c] = axy[c].value();
-        dxx[c] = axx[c].value();
+        dyy[c] = (DM & 1) ? ayy[(DM & 1) ? c : 0].value() : 0.0;
+        dxy[c] = (DM & 2) ? axy[(DM & 2) ? c : 0].value() : 0.0;
+        dxx[c] = (DM & 4) ? axx[(DM & 4) ? c : 0].value() : 0.0;
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
-            dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
-            dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
-            dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
+            if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
+            if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
+            if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
         }
     }
     if (lane < G) {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             int k = k0 + c;
-            if (k < M.w) {
+            if (k < w) {
                 part[0 * kBatchMaxW + k] = dyy[c];
                 part[1 * kBatchMaxW + k] = dxy[c];
                 part[2 * kBatchMaxW + k] = dxx[c];
@@ -168,31 +216,38 @@ __host__ __device__ constexpr int batch_max_cpl(int xsize) { return xsize == 8 ?
 #define SP_BATCH_MINB 4
 #endif
 
-template <class VT, class XT>
+template <class VT, class XT, int DM>
 __global__ void __launch_bounds__(kSpmvThreads, SP_BATCH_MINB) k_spmmv_batched(const __grid_constant__ BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
     const int T = gridDim.x * kSpmvWarps;
-    for (int u = gw; u < a.nunits; u += T) {
+    for (int u = gw;;) {
+        if (SP_BATCH_DYNAMIC) {
+            int t = 0;
+            if (lane == 0) t = (int)atomicAdd(a.next, 1u);
+            u = __shfl_sync(0xffffffffu, t, 0);
+        }
+        if (u >= a.nunits) break;
         const BUnit U = a.units[u];
-        const BMat M = a.mats[U.m];
+        const BMat *__restrict__ M = a.mats + U.m;
         double *part = a.partials + (int64_t)u * 3 * kBatchMaxW;
         constexpr bool wide = batch_max_cpl(sizeof(XT)) >= 4;
         switch (U.variant) {
-            case 0: batch_unit<VT, XT, 1, 1>(a, M, U, lane, part); break;
-            case 1: batch_unit<VT, XT, 2, 1>(a, M, U, lane, part); break;
-            case 2: batch_unit<VT, XT, 2, 2>(a, M, U, lane, part); break;
-            case 3: batch_unit<VT, XT, 4, 1>(a, M, U, lane, part); break;
-            case 4: batch_unit<VT, XT, 4, 2>(a, M, U, lane, part); break;
-            case 6: batch_unit<VT, XT, 8, 1>(a, M, U, lane, part); break;
-            case 7: batch_unit<VT, XT, 8, 2>(a, M, U, lane, part); break;
+            case 0: batch_unit<VT, XT, 1, 1, DM>(a, M, U, lane, part); break;
+            case 1: batch_unit<VT, XT, 2, 1, DM>(a, M, U, lane, part); break;
+            case 2: batch_unit<VT, XT, 2, 2, DM>(a, M, U, lane, part); break;
+            case 3: batch_unit<VT, XT, 4, 1, DM>(a, M, U, lane, part); break;
+            case 4: batch_unit<VT, XT, 4, 2, DM>(a, M, U, lane, part); break;
+            case 6: batch_unit<VT, XT, 8, 1, DM>(a, M, U, lane, part); break;
+            case 7: batch_unit<VT, XT, 8, 2, DM>(a, M, U, lane, part); break;
             default:
                 if constexpr (wide) {
-                    if (U.variant == 5) batch_unit<VT, XT, 4, 4>(a, M, U, lane, part);
-                    else batch_unit<VT, XT, 8, 4>(a, M, U, lane, part);
+                    if (U.variant == 5) batch_unit<VT, XT, 4, 4, DM>(a, M, U, lane, part);
+                    else batch_unit<VT, XT, 8, 4, DM>(a, M, U, lane, part);
                 }
                 break;
         }
+        if (!SP_BATCH_DYNAMIC) u += T;
     }
 }
 
@@ -226,7 +281,7 @@ struct Batch {
     std::vector<sp_mat *> mats;       // not owned
     std::vector<BMat> hmats;
     std::vector<BUnit> hunits;
-    DevBufPtr dmats, dunits, partials;
+    DevBufPtr dmats, dunits, partials, next;
     int grid = 1;
 };
 
@@ -310,21 +365,22 @@ static int batch_init(Batch &B, int count, sp_mat *const *A, const int32_t *widt
     SP_TRY(device_sm_count(&sms));
     int occ = 1;
     if (B.vdt == SP_F64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<double, double>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<double, double, 7>, kSpmvThreads, 0);
     else if (xdt == SP_F32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, float>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, float, 7>, kSpmvThreads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, double>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, double, 7>, kSpmvThreads, 0);
     cudaGetLastError();
     occ = std::max(1, occ);
     B.grid = sms * occ;
     int64_t warps = (int64_t)B.grid * kSpmvWarps;
     // about 4 units per resident warp, at least 32 slots each
-    int64_t target = std::max<int64_t>(1, total_cost / (warps * 4));
+    int64_t target = std::max<int64_t>(1, total_cost / (warps * SP_BATCH_UNITS_PER_WARP));
     SP_TRY(make_units(B, target));
     SP_TRY(dev_alloc(B.dmats, count * sizeof(BMat), nullptr));
     SP_TRY(dev_alloc(B.dunits, std::max<size_t>(1, B.hunits.size()) * sizeof(BUnit), nullptr));
     SP_TRY(dev_alloc(B.partials, std::max<size_t>(1, B.hunits.size()) * 3 * kBatchMaxW * sizeof(double), nullptr));
+    SP_TRY(dev_alloc(B.next, sizeof(unsigned), nullptr));
     SP_CUDA(cudaMemset(B.partials->ptr, 0, B.partials->bytes));
     SP_CUDA(cudaMemcpy(B.dunits->ptr, B.hunits.data(), B.hunits.size() * sizeof(BUnit), cudaMemcpyHostToDevice));
     return SP_OK;
@@ -336,6 +392,16 @@ static int batch_upload(Batch &B, cudaStream_t s) {
     return SP_OK;
 }
 
+template <class VT, class XT>
+static void launch_batched_dm(int dm, int grid, const BatchArgs &a, cudaStream_t s) {
+    if (dm == 0)
+        k_spmmv_batched<VT, XT, 0><<<grid, kSpmvThreads, 0, s>>>(a);
+    else if (dm == 6)
+        k_spmmv_batched<VT, XT, 6><<<grid, kSpmvThreads, 0, s>>>(a);
+    else
+        k_spmmv_batched<VT, XT, 7><<<grid, kSpmvThreads, 0, s>>>(a);
+}
+
 static int batch_launch(const Batch &B, uint32_t flags, double alpha, double beta, cudaStream_t s) {
     BatchArgs a;
     a.mats = (const BMat *)B.dmats->ptr;
@@ -345,13 +411,18 @@ static int batch_launch(const Batch &B, uint32_t flags, double alpha, double bet
     a.alpha = alpha;
     a.beta = beta;
     a.partials = (double *)B.partials->ptr;
+    a.next = (unsigned *)B.next->ptr;
+    if (SP_BATCH_DYNAMIC) SP_CUDA(cudaMemsetAsync(B.next->ptr, 0, sizeof(unsigned), s));
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.grid, (a.nunits + kSpmvWarps - 1) / kSpmvWarps));
+    // dot set compiled in: none, the CG pair <x,y>, <x,x>, or all three
+    const int req = (int)((flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY);
+    const int dm = req == 0 ? 0 : (req & 1) ? 7 : 6;
     if (B.vdt == SP_F64 && B.xdt == SP_F64)
-        k_spmmv_batched<double, double><<<grid, kSpmvThreads, 0, s>>>(a);
+        launch_batched_dm<double, double>(dm, grid, a, s);
     else if (B.vdt == SP_F32 && B.xdt == SP_F32)
-        k_spmmv_batched<float, float><<<grid, kSpmvThreads, 0, s>>>(a);
+        launch_batched_dm<float, float>(dm, grid, a, s);
     else if (B.vdt == SP_F32 && B.xdt == SP_F64)
-        k_spmmv_batched<float, double><<<grid, kSpmvThreads, 0, s>>>(a);
+        launch_batched_dm<float, double>(dm, grid, a, s);
     else
         return SP_ERR_DTYPE;
     SP_CUDA(cudaGetLastError());
@@ -414,30 +485,79 @@ __global__ void k_cg_scalars(const BMat *mats, const double *partials, int count
     coef_f[m * kBatchMaxW + k] = make_float2((float)alpha, (float)beta);
 }
 
+// 16-byte vector of the inner precision
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+};
+
+template <class T>
+__device__ __forceinline__ void cg_update_elem(T &re, T se, T &pe, T &qe, T &de, T alpha, T beta) {
+    pe = re + beta * pe;
+    qe = se + beta * qe;
+    de = de + alpha * pe;
+    re = re - alpha * qe;
+}
+
+// p = r + beta p, q = s + beta q, d = d + alpha p, r = r - alpha q with the
+// (alpha, beta) of each element's column; 16-byte accesses (units start at a
+// multiple of 16 bytes and of a row), the unit's last partial vector scalar.
 template <class T>
 __global__ void k_cg_update(const VUnit *units, int nunits, const CGVec *vec, const double *coef,
                             const float2 *coef_f) {
+    constexpr int NV = 16 / sizeof(T);
+    using V = typename Vec16<T>::V;
+    auto ab_of = [&](int m, int k, T &alpha, T &beta) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 ab = coef_f[m * kBatchMaxW + k];  // no float64 conversion per element
+            alpha = ab.x;
+            beta = ab.y;
+        } else {
+            alpha = coef[(m * kBatchMaxW + k) * 2];
+            beta = coef[(m * kBatchMaxW + k) * 2 + 1];
+        }
+    };
     for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
         const VUnit U = units[u];
-        const CGVec V = vec[U.m];
-        T *r = (T *)V.r, *s = (T *)V.s, *p = (T *)V.p, *q = (T *)V.q, *d = (T *)V.d;
-        for (int64_t e = U.e0 + threadIdx.x; e < U.e1; e += blockDim.x) {
-            const int k = (int)(e - U.e0) % U.w;  // units start on a row boundary
-            T alpha, beta;
-            if constexpr (sizeof(T) == 4) {
-                const float2 ab = coef_f[U.m * kBatchMaxW + k];  // no float64 conversion per element
-                alpha = ab.x;
-                beta = ab.y;
-            } else {
-                alpha = coef[(U.m * kBatchMaxW + k) * 2];
-                beta = coef[(U.m * kBatchMaxW + k) * 2 + 1];
+        const CGVec Vc = vec[U.m];
+        T *r = (T *)Vc.r + U.e0, *s = (T *)Vc.s + U.e0, *p = (T *)Vc.p + U.e0, *q = (T *)Vc.q + U.e0,
+          *d = (T *)Vc.d + U.e0;
+        const int64_t n = U.e1 - U.e0;
+        const int64_t nv = n / NV;
+        for (int64_t t = threadIdx.x; t < nv; t += blockDim.x) {
+            V rv = reinterpret_cast<const V *>(r)[t], sv = reinterpret_cast<const V *>(s)[t];
+            V pv = reinterpret_cast<const V *>(p)[t], qv = reinterpret_cast<const V *>(q)[t];
+            V dv = reinterpret_cast<const V *>(d)[t];
+            T *re = reinterpret_cast<T *>(&rv), *se = reinterpret_cast<T *>(&sv), *pe = reinterpret_cast<T *>(&pv);
+            T *qe = reinterpret_cast<T *>(&qv), *de = reinterpret_cast<T *>(&dv);
+            int k = (int)((t * NV) % U.w);  // units start on a row boundary
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                T alpha, beta;
+                ab_of(U.m, k, alpha, beta);
+                cg_update_elem(re[j], se[j], pe[j], qe[j], de[j], alpha, beta);
+                k = k + 1 == U.w ? 0 : k + 1;
             }
-            T pe = r[e] + beta * p[e];
-            T qe = s[e] + beta * q[e];
+            reinterpret_cast<V *>(p)[t] = pv;
+            reinterpret_cast<V *>(q)[t] = qv;
+            reinterpret_cast<V *>(d)[t] = dv;
+            reinterpret_cast<V *>(r)[t] = rv;
+        }
+        for (int64_t e = nv * NV + threadIdx.x; e < n; e += blockDim.x) {
+            T alpha, beta;
+            ab_of(U.m, (int)(e % U.w), alpha, beta);
+            T re = r[e], pe = p[e], qe = q[e], de = d[e];
+            cg_update_elem(re, s[e], pe, qe, de, alpha, beta);
             p[e] = pe;
             q[e] = qe;
-            d[e] = d[e] + alpha * pe;
-            r[e] = r[e] - alpha * qe;
+            d[e] = de;
+            r[e] = re;
         }
     }
 }
@@ -662,7 +782,9 @@ int sp_cg_create(sp_cg **out, int count, sp_mat *const *A, const int32_t *widths
     // element units for the vector kernels (about 16K elements each)
     for (int m = 0; m < count && rc == SP_OK; ++m) {
         int64_t n = cg->nrows[m] * widths[m];
-        const int64_t step = 16384 / widths[m] * widths[m];
+        // a multiple of the row width and of 4 elements: every unit starts on a
+        // row and on a 16-byte boundary
+        const int64_t step = 16384 / (4 * widths[m]) * (4 * widths[m]);
         for (int64_t e = 0; e < n; e += step) cg->hvunits.push_back(VUnit{m, widths[m], e, std::min(n, e + step)});
     }
     if (rc == SP_OK) rc = dev_alloc(cg->dvunits, std::max<size_t>(1, cg->hvunits.size()) * sizeof(VUnit), cs);
