@@ -179,28 +179,29 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
         }
         cur = nxt;
     }
-    if constexpr (!dots) return;
-    double dyy[CPL], dxy[CPL], dxx[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-        dyy[c] = (DM & 1) ? ayy[(DM & 1) ? c : 0].value() : 0.0;
-        dxy[c] = (DM & 2) ? axy[(DM & 2) ? c : 0].value() : 0.0;
-        dxx[c] = (DM & 4) ? axx[(DM & 4) ? c : 0].value() : 0.0;
-#pragma unroll
-        for (int o = G; o < 32; o <<= 1) {
-            if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
-            if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
-            if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
-        }
-    }
-    if (lane < G) {
+    if constexpr (dots) {
+        double dyy[CPL], dxy[CPL], dxx[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-            int k = k0 + c;
-            if (k < w) {
-                part[0 * kBatchMaxW + k] = dyy[c];
-                part[1 * kBatchMaxW + k] = dxy[c];
-                part[2 * kBatchMaxW + k] = dxx[c];
+            dyy[c] = (DM & 1) ? ayy[(DM & 1) ? c : 0].value() : 0.0;
+            dxy[c] = (DM & 2) ? axy[(DM & 2) ? c : 0].value() : 0.0;
+            dxx[c] = (DM & 4) ? axx[(DM & 4) ? c : 0].value() : 0.0;
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) {
+                if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
+                if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
+                if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
+            }
+        }
+        if (lane < G) {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                int k = k0 + c;
+                if (k < w) {
+                    part[0 * kBatchMaxW + k] = dyy[c];
+                    part[1 * kBatchMaxW + k] = dxy[c];
+                    part[2 * kBatchMaxW + k] = dxx[c];
+                }
             }
         }
     }
