@@ -361,15 +361,19 @@ int fill_values_from_csr(const Pattern &P, sp_dtype vdt, void *val_sell, const v
 
 // ------------------------------------------------------------------ static work partition
 
-// cost of each 32-slot block: stored-entry work of its rows + 2 per real row
-// (the epilogue); slots >= nrows are padding rows
+// cost of each 32-slot block: stored-entry work of its rows + SP_ROW_COST per
+// real row (the epilogue and the fixed latency of a row); slots >= nrows are
+// padding rows
+#ifndef SP_ROW_COST
+#define SP_ROW_COST 16
+#endif
 __global__ void k_block32_cost(const int32_t *__restrict__ slotlen, int64_t nslots, int64_t nrows,
                                int64_t nb32, int64_t *__restrict__ cost) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb32;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t c = 0;
         int64_t e = min(32 * k + 32, nslots);
-        for (int64_t s = 32 * k; s < e; ++s) c += slotlen[s] + (s < nrows ? 2 : 0);
+        for (int64_t s = 32 * k; s < e; ++s) c += slotlen[s] + (s < nrows ? SP_ROW_COST : 0);
         cost[k] = c;
     }
 }
