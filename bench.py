@@ -168,6 +168,10 @@ def run_ours(args, rank, world):
     W = WORKLOAD
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        # one small build first, so the timed build excludes one-time module loading
+        from workloads import generators as _gen
+        sellcs.SellMatrix(_gen.laplace2d(8, 0.0), C=W["C"], sigma=W["sigma"], dtype="f64").close()
+        torch.cuda.synchronize()
         t0 = time.time()
         mat = sellcs.SellMatrix(A, C=W["C"], sigma=W["sigma"], dtype="f64")
         torch.cuda.synchronize()
@@ -216,36 +220,35 @@ def run_ours(args, rank, world):
             ms = float(t.item())
             ms_step = ms / args.steps
 
-        # e2e: host (pinned) buffers, H2D of x, y, z and D2H of y, z, dots inside the timed region
+        # e2e: the library's host-buffer entry point (sp_spmv_host on a host plan):
+        # every step copies x, y, z in from page-locked host memory and y, z and
+        # the dots back, inside the timed region; consecutive steps overlap their
+        # copies with the product of the step between them
         hx_h = torch.from_numpy(X).pin_memory()
         hy_h = torch.from_numpy(Y0).pin_memory()
         hz_h = torch.from_numpy(Z0).pin_memory()
         oy = torch.empty_like(hy_h).pin_memory()
         oz = torch.empty_like(hz_h).pin_memory()
         od = torch.empty(3, dtype=torch.float64).pin_memory()
+        plan = sellcs.HostPlan(mat, 1, "f64")
+        kw = dict(alpha=WORKLOAD["alpha"], gamma=WORKLOAD["gamma"], beta=WORKLOAD["beta"], dot_xy=True, dot_yy=True,
+                  delta=WORKLOAD["delta"], eta=WORKLOAD["eta"])
 
         def e2e_step():
-            x.copy_(hx_h, non_blocking=True)
-            y.copy_(hy_h, non_blocking=True)
-            z.copy_(hz_h, non_blocking=True)
-            step()
-            oy.copy_(y, non_blocking=True)
-            oz.copy_(z, non_blocking=True)
-            od.copy_(dot, non_blocking=True)
+            plan.spmv(hx_h, oy, y_in=hy_h, z_in=hz_h, z_out=oz, dot=od, **kw)
 
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(3, args.warmup)):
             e2e_step()
-        stream.synchronize()
-        e2e_steps = max(3, min(args.steps, 20))
-        ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev2.record(stream)
+        plan.sync()
+        e2e_steps = max(3, min(args.steps, 200))
+        t0 = time.perf_counter()
         for _ in range(e2e_steps):
             e2e_step()
-        ev3.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = ev2.elapsed_time(ev3) / e2e_steps
+        plan.sync()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        plan.close()
         h2d = X.nbytes + Y0.nbytes + Z0.nbytes
-        d2h = Y0.nbytes + Z0.nbytes + 3 * 8
+        d2h = Y0.nbytes + Z0.nbytes + 2 * 8
         for h in (hx, hy, hz):
             sellcs.sp_dense_destroy(h)
 
@@ -282,7 +285,9 @@ def run_ours(args, rank, world):
                        l2="inputs 0.96 GB > 129 MB L2, no flush", parallelism=f"replicas{world}"),
         "roofline": roof,
         "e2e": {"value": round(nbytes / (e2e_ms * 1e-3) / 1e9 * world, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4),
+                "api": "sp_spmv_host on a host plan (pinned buffers, copies of consecutive steps overlapped)",
+                "steps": e2e_steps},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "setup": {"sell_build_s": round(setup_s, 4), "in_spmv_calls": round(setup_s / (ms_step * 1e-3), 1)},

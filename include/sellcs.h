@@ -231,6 +231,42 @@ SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spm
 SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
                     void *stream);
 
+/* ------------------------------------------------------------------ host block vectors */
+
+/*
+ * Pipelined products over block vectors in HOST memory (no counterpart in the
+ * paper: the end-to-end form of sp_spmv for callers whose vectors live on the
+ * host).  A plan owns two sets of device buffers for x, y, z and the dots and
+ * three streams (copy-in, product, copy-out); call k uses set k mod 2, so the
+ * copy-in of call k+1 and the copy-out of call k-1 overlap the product of call
+ * k.  The product is sp_spmv's, with the same results.
+ *   sp_host_plan_create   A: the matrix (not owned; it must outlive the plan);
+ *                         w >= 1 block width; vec_dtype SP_F64 or SP_F32 (SP_F64
+ *                         when A holds float64 values).  Allocates
+ *                         2 * (ncols + 2 nrows) * w elements of device memory and
+ *                         synchronises the device.
+ *   sp_spmv_host          x: ncols x w, row-major, read; y_in: nrows x w, read when
+ *                         opts has SP_SPMV_AXPBY (else may be NULL); y_out: nrows x w,
+ *                         written; z_in / z_out: read / written with
+ *                         SP_SPMV_CHAIN_AXPBY (opts->z is ignored); dot: 3 w host
+ *                         doubles, the requested slots written (opts->dot is ignored).
+ *                         Every pointer is host memory; page-locked memory gives
+ *                         the overlap (pageable memory works but serialises).  The
+ *                         call only enqueues: the caller must not touch any of the
+ *                         buffers until sp_host_plan_sync returns, and a call whose
+ *                         y_in (z_in) is an earlier call's y_out (z_out) needs a
+ *                         sync in between.  Errors of the enqueued work surface at
+ *                         sp_host_plan_sync.
+ *   sp_host_plan_sync     waits for every enqueued call.
+ *   sp_host_plan_destroy  waits, then frees the plan.
+ */
+typedef struct sp_host_plan sp_host_plan;
+SP_API int sp_host_plan_create(sp_host_plan **out, const sp_mat *A, int32_t w, sp_dtype vec_dtype);
+SP_API int sp_spmv_host(sp_host_plan *p, const void *x, const void *y_in, void *y_out, const void *z_in,
+                        void *z_out, double *dot, const sp_spmv_opts *opts);
+SP_API int sp_host_plan_sync(sp_host_plan *p);
+SP_API int sp_host_plan_destroy(sp_host_plan *p);
+
 /* ------------------------------------------------------------------ batched SpMMV */
 
 /*

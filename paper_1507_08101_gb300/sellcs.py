@@ -108,6 +108,10 @@ _SIGS = {
     "sp_cg_destroy": (I, [P, P]),
     "sp_spmv_noalloc": (I, [P, I, P, P, P, P, I64, I64, I32, P, I64, P, I64, P, I64, I32, I, ct.c_uint32,
                             ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.c_double, ct.c_double, P, P]),
+    "sp_host_plan_create": (I, [PP, P, I32, I]),
+    "sp_spmv_host": (I, [P, P, P, P, P, P, P, ct.POINTER(sp_spmv_opts)]),
+    "sp_host_plan_sync": (I, [P]),
+    "sp_host_plan_destroy": (I, [P]),
 }
 
 
@@ -401,6 +405,59 @@ def spmv(A: SellMatrix, x, y, *, alpha=None, gamma=None, beta=None, dot_yy=False
         if hz is not None:
             L.sp_dense_destroy(hz, None)
     return dot
+
+
+def _host_ptr(a):
+    """Address of a host (CPU) array: torch CPU tensor or numpy array, or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda, "host plan buffers live in host memory"
+        return ct.c_void_p(a.data_ptr())
+    return ct.c_void_p(a.ctypes.data)
+
+
+class HostPlan:
+    """Pipelined products over block vectors in host memory (sp_host_plan_*).
+
+    ``spmv`` only enqueues (copy-in, product, copy-out on the plan's streams);
+    the host buffers must stay untouched until ``sync``.  Page-locked buffers
+    (torch ``pin_memory()``) let the copies of consecutive calls overlap."""
+
+    def __init__(self, A: SellMatrix, w: int, vec_dtype: str = "f64"):
+        self._lib = lib()
+        self.A = A
+        self.w = int(w)
+        h = ct.c_void_p()
+        check(self._lib.sp_host_plan_create(ct.byref(h), A.handle, self.w, DTYPES[vec_dtype]), "sp_host_plan_create")
+        self.handle = h
+        self._keep = []
+
+    def spmv(self, x, y_out, *, y_in=None, alpha=None, gamma=None, beta=None, dot_yy=False, dot_xy=False,
+             dot_xx=False, z_in=None, z_out=None, delta=None, eta=None, dot=None):
+        o, keep = make_opts(self.w, alpha=alpha, gamma=gamma, beta=beta, dot_yy=dot_yy, dot_xy=dot_xy, dot_xx=dot_xx)
+        if z_in is not None:
+            o.flags |= SP_SPMV_CHAIN_AXPBY
+            o.delta, o.eta = float(delta), float(eta)
+        self._keep.append((x, y_in, y_out, z_in, z_out, dot))
+        check(self._lib.sp_spmv_host(self.handle, _host_ptr(x), _host_ptr(y_in), _host_ptr(y_out), _host_ptr(z_in),
+                                     _host_ptr(z_out), _host_ptr(dot), ct.byref(o)), "sp_spmv_host")
+
+    def sync(self):
+        check(self._lib.sp_host_plan_sync(self.handle), "sp_host_plan_sync")
+        self._keep.clear()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sp_host_plan_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def spmv_adjoint(A: SellMatrix, g, x=None, dx=None, dvals=None, stream=None):

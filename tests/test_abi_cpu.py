@@ -56,6 +56,10 @@ def test_host_argument_checks(L):
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 7, 0, None) == s.SP_ERR_DTYPE
     assert L.sp_mat_create_csr(ct.byref(h), -1, 1, rp, None, None, 32, 1, 0, 0, None) == s.SP_ERR_DIM
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 0, 1 << 9, None) == s.SP_ERR_ARG
+    assert L.sp_host_plan_create(None, None, 1, s.SP_F64) == s.SP_ERR_ARG
+    assert L.sp_spmv_host(None, None, None, None, None, None, None, None) == s.SP_ERR_ARG
+    assert L.sp_host_plan_sync(None) == s.SP_ERR_ARG
+    assert L.sp_host_plan_destroy(None) == s.SP_ERR_ARG
     both = s.SP_MAT_ORDER_FRONT | s.SP_MAT_ORDER_RANGES  # at most one work order
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 0, both, None) == s.SP_ERR_ARG
     # dense views: ld too small, bf16 vectors, null pointer
