@@ -212,16 +212,21 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
 // every layout
 __host__ __device__ constexpr int batch_max_cpl(int xsize) { return xsize == 8 ? 2 : 4; }
 
-// minimum resident blocks per SM requested for the batched kernel (knob)
-#ifndef SP_BATCH_MINB
-#define SP_BATCH_MINB 4
+// block size and minimum resident blocks per SM of the batched kernel (knobs)
+#ifndef SP_BATCH_THREADS
+#define SP_BATCH_THREADS 256
 #endif
+#ifndef SP_BATCH_MINB
+#define SP_BATCH_MINB (1024 / SP_BATCH_THREADS)
+#endif
+constexpr int kBatchThreads = SP_BATCH_THREADS;
+constexpr int kBatchWarps = kBatchThreads / 32;
 
 template <class VT, class XT, int DM>
-__global__ void __launch_bounds__(kSpmvThreads, SP_BATCH_MINB) k_spmmv_batched(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) k_spmmv_batched(const __grid_constant__ BatchArgs a) {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
-    const int T = gridDim.x * kSpmvWarps;
+    const int gw = blockIdx.x * kBatchWarps + (threadIdx.x >> 5);
+    const int T = gridDim.x * kBatchWarps;
     for (int u = gw;;) {
         if (SP_BATCH_DYNAMIC) {
             int t = 0;
@@ -366,15 +371,15 @@ static int batch_init(Batch &B, int count, sp_mat *const *A, const int32_t *widt
     SP_TRY(device_sm_count(&sms));
     int occ = 1;
     if (B.vdt == SP_F64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<double, double, 7>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<double, double, 7>, kBatchThreads, 0);
     else if (xdt == SP_F32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, float, 7>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, float, 7>, kBatchThreads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, double, 7>, kSpmvThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv_batched<float, double, 7>, kBatchThreads, 0);
     cudaGetLastError();
     occ = std::max(1, occ);
     B.grid = sms * occ;
-    int64_t warps = (int64_t)B.grid * kSpmvWarps;
+    int64_t warps = (int64_t)B.grid * kBatchWarps;
     // about 4 units per resident warp, at least 32 slots each
     int64_t target = std::max<int64_t>(1, total_cost / (warps * SP_BATCH_UNITS_PER_WARP));
     SP_TRY(make_units(B, target));
@@ -396,11 +401,11 @@ static int batch_upload(Batch &B, cudaStream_t s) {
 template <class VT, class XT>
 static void launch_batched_dm(int dm, int grid, const BatchArgs &a, cudaStream_t s) {
     if (dm == 0)
-        k_spmmv_batched<VT, XT, 0><<<grid, kSpmvThreads, 0, s>>>(a);
+        k_spmmv_batched<VT, XT, 0><<<grid, kBatchThreads, 0, s>>>(a);
     else if (dm == 6)
-        k_spmmv_batched<VT, XT, 6><<<grid, kSpmvThreads, 0, s>>>(a);
+        k_spmmv_batched<VT, XT, 6><<<grid, kBatchThreads, 0, s>>>(a);
     else
-        k_spmmv_batched<VT, XT, 7><<<grid, kSpmvThreads, 0, s>>>(a);
+        k_spmmv_batched<VT, XT, 7><<<grid, kBatchThreads, 0, s>>>(a);
 }
 
 static int batch_launch(const Batch &B, uint32_t flags, double alpha, double beta, cudaStream_t s) {
@@ -414,7 +419,7 @@ static int batch_launch(const Batch &B, uint32_t flags, double alpha, double bet
     a.partials = (double *)B.partials->ptr;
     a.next = (unsigned *)B.next->ptr;
     if (SP_BATCH_DYNAMIC) SP_CUDA(cudaMemsetAsync(B.next->ptr, 0, sizeof(unsigned), s));
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.grid, (a.nunits + kSpmvWarps - 1) / kSpmvWarps));
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.grid, (a.nunits + kBatchWarps - 1) / kBatchWarps));
     // dot set compiled in: none, the CG pair <x,y>, <x,x>, or all three
     const int req = (int)((flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY);
     const int dm = req == 0 ? 0 : (req & 1) ? 7 : 6;
