@@ -86,6 +86,9 @@ struct SpmvArgs {
 #ifndef SP_UNROLL_WIDE
 #define SP_UNROLL_WIDE 2
 #endif
+#ifndef SP_UNROLL_WIDE_F32
+#define SP_UNROLL_WIDE_F32 4
+#endif
 #ifndef SP_MINB_W1
 #define SP_MINB_W1 1
 #endif
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
-    constexpr int U = CPL >= 4 ? SP_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
+    constexpr int U = CPL >= 4 ? (sizeof(XT) == 4 ? SP_UNROLL_WIDE_F32 : SP_UNROLL_WIDE) : SP_UNROLL_NARROW / CPL;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
