@@ -236,10 +236,10 @@ SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_
 /*
  * Pipelined products over block vectors in HOST memory (no counterpart in the
  * paper: the end-to-end form of sp_spmv for callers whose vectors live on the
- * host).  A plan owns two sets of device buffers for x, y, z and the dots and
- * three streams (copy-in, product, copy-out); call k uses set k mod 2, so the
- * copy-in of call k+1 and the copy-out of call k-1 overlap the product of call
- * k.  The product is sp_spmv's, with the same results.
+ * host).  A plan owns three sets of device buffers for x, y, z and the dots
+ * and three streams (copy-in, product, copy-out); call k uses set k mod 3, so
+ * the copy-in of call k+1 and the copy-out of call k-1 overlap the product of
+ * call k.  The product is sp_spmv's, with the same results.
  *   sp_host_plan_create   A: the matrix (not owned; it must outlive the plan);
  *                         w >= 1 block width; vec_dtype SP_F64 or SP_F32 (SP_F64
  *                         when A holds float64 values).  Allocates

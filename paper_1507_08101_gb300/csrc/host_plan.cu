@@ -1,9 +1,9 @@
 // Pipelined augmented product over block vectors in HOST memory.
 //
-// A plan owns two sets of device buffers (x, y, z, dots) and three streams:
-// copy-in, product, copy-out.  Call k uses set k mod 2: its copy-in waits
-// until the copy-out of call k - 2 (the last user of that set) is done, the
-// product waits for its copy-in, the copy-out for its product.  So the
+// A plan owns kSets sets of device buffers (x, y, z, dots) and three streams:
+// copy-in, product, copy-out.  Call k uses set k mod kSets: its copy-in waits
+// until the copy-out of call k - kSets (the last user of that set) is done,
+// the product waits for its copy-in, the copy-out for its product.  So the
 // copy-in of call k + 1 and the copy-out of call k - 1 run while the product
 // of call k runs, in both directions of the host link at once.  The product
 // is sp_spmv itself, so the results are those of sp_spmv on the same inputs.
@@ -13,16 +13,21 @@
 
 using sp::DevBufPtr;
 
+#ifndef SP_HOST_PLAN_SETS
+#define SP_HOST_PLAN_SETS 3
+#endif
+constexpr int kSets = SP_HOST_PLAN_SETS;
+
 struct sp_host_plan {
     const sp_mat *A = nullptr;
     int w = 0;
     sp_dtype xdt = SP_F64;
     size_t xs = 8;
-    sp_dense *dx[2] = {nullptr, nullptr}, *dy[2] = {nullptr, nullptr}, *dz[2] = {nullptr, nullptr};
-    DevBufPtr ddot[2];
+    sp_dense *dx[kSets] = {}, *dy[kSets] = {}, *dz[kSets] = {};
+    DevBufPtr ddot[kSets];
     cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
-    cudaEvent_t in_done[2] = {nullptr, nullptr}, comp_done[2] = {nullptr, nullptr}, out_done[2] = {nullptr, nullptr};
-    bool used[2] = {false, false};
+    cudaEvent_t in_done[kSets] = {}, comp_done[kSets] = {}, out_done[kSets] = {};
+    bool used[kSets] = {};
     int next = 0;
 };
 
@@ -31,7 +36,7 @@ static void plan_free(sp_host_plan *p) {
     if (p->in) cudaStreamSynchronize(p->in);
     if (p->comp) cudaStreamSynchronize(p->comp);
     if (p->out) cudaStreamSynchronize(p->out);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kSets; ++b) {
         if (p->dx[b]) sp_dense_destroy(p->dx[b], nullptr);
         if (p->dy[b]) sp_dense_destroy(p->dy[b], nullptr);
         if (p->dz[b]) sp_dense_destroy(p->dz[b], nullptr);
@@ -58,7 +63,7 @@ int sp_host_plan_create(sp_host_plan **out, const sp_mat *A, int32_t w, sp_dtype
     p->xdt = vec_dtype;
     p->xs = vec_dtype == SP_F64 ? 8 : 4;
     int rc = SP_OK;
-    for (int b = 0; b < 2 && rc == SP_OK; ++b) {
+    for (int b = 0; b < kSets && rc == SP_OK; ++b) {
         rc = sp_dense_create(&p->dx[b], P.ncols, w, vec_dtype, SP_ROW_MAJOR, nullptr);
         if (rc == SP_OK) rc = sp_dense_create(&p->dy[b], P.nrows, w, vec_dtype, SP_ROW_MAJOR, nullptr);
         if (rc == SP_OK) rc = sp_dense_create(&p->dz[b], P.nrows, w, vec_dtype, SP_ROW_MAJOR, nullptr);
@@ -68,7 +73,7 @@ int sp_host_plan_create(sp_host_plan **out, const sp_mat *A, int32_t w, sp_dtype
     if (rc == SP_OK) e = cudaStreamCreateWithFlags(&p->in, cudaStreamNonBlocking);
     if (rc == SP_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->comp, cudaStreamNonBlocking);
     if (rc == SP_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->out, cudaStreamNonBlocking);
-    for (int b = 0; b < 2 && rc == SP_OK && e == cudaSuccess; ++b) {
+    for (int b = 0; b < kSets && rc == SP_OK && e == cudaSuccess; ++b) {
         e = cudaEventCreateWithFlags(&p->in_done[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->comp_done[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->out_done[b], cudaEventDisableTiming);
@@ -99,7 +104,7 @@ int sp_spmv_host(sp_host_plan *p, const void *x, const void *y_in, void *y_out, 
     const sp::Pattern &P = *p->A->pat;
     const size_t xbytes = (size_t)P.ncols * p->w * p->xs, ybytes = (size_t)P.nrows * p->w * p->xs;
     const int b = p->next;
-    p->next ^= 1;
+    p->next = (p->next + 1) % kSets;
     int rc = SP_OK;
     // copy-in (after the copy-out of the last call that used this buffer set)
     if (p->used[b]) SP_CUDA(cudaStreamWaitEvent(p->in, p->out_done[b], 0));
