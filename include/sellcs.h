@@ -243,7 +243,7 @@ SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_
  *   sp_host_plan_create   A: the matrix (not owned; it must outlive the plan);
  *                         w >= 1 block width; vec_dtype SP_F64 or SP_F32 (SP_F64
  *                         when A holds float64 values).  Allocates
- *                         2 * (ncols + 2 nrows) * w elements of device memory and
+ *                         3 * (ncols + 2 nrows) * w elements of device memory and
  *                         synchronises the device.
  *   sp_spmv_host          x: ncols x w, row-major, read; y_in: nrows x w, read when
  *                         opts has SP_SPMV_AXPBY (else may be NULL); y_out: nrows x w,
