@@ -30,7 +30,7 @@ def _inputs(A, w, k, tdt):
 
 
 @pytest.mark.parametrize("vdt,xdt", [("f64", "f64"), ("f32", "f32")])
-@pytest.mark.parametrize("w", [1, 4])
+@pytest.mark.parametrize("w", [1, 4, 33])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_plan_matches_device_product(cuda_ok, matrix, vdt, xdt, w, pinned):
     A = matrix
