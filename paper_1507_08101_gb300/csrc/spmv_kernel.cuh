@@ -457,11 +457,21 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 #endif
 // Latency overlap in the slot loop: issue the epilogue's loads before the row
 // loop, and load the next slot's metadata while the current slot runs.
-#ifndef SP_EARLY_EPI
-#define SP_EARLY_EPI 1
+// Per vector precision: the float64 kernels are register bound, and the
+// epilogue's early loads and the next slot's metadata cost them more than they
+// hide (bench workload +4 %, Laplacian 256^3 +6 % without); the float32
+// kernels gain from both.
+#ifndef SP_EARLY_EPI_F64
+#define SP_EARLY_EPI_F64 0
 #endif
-#ifndef SP_PREFETCH_META
-#define SP_PREFETCH_META 1
+#ifndef SP_EARLY_EPI_F32
+#define SP_EARLY_EPI_F32 1
+#endif
+#ifndef SP_PREFETCH_META_F64
+#define SP_PREFETCH_META_F64 0
+#endif
+#ifndef SP_PREFETCH_META_F32
+#define SP_PREFETCH_META_F32 1
 #endif
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
@@ -474,6 +484,8 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
     constexpr int U = CPL >= 4 ? (sizeof(XT) == 4 ? SP_UNROLL_WIDE_F32 : SP_UNROLL_WIDE) : SP_UNROLL_NARROW / CPL;
+    constexpr bool early_epi = sizeof(XT) == 8 ? SP_EARLY_EPI_F64 != 0 : SP_EARLY_EPI_F32 != 0;
+    constexpr bool prefetch_meta = sizeof(XT) == 8 ? SP_PREFETCH_META_F64 != 0 : SP_PREFETCH_META_F32 != 0;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
@@ -530,7 +542,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         const bool epi_lane = (!MT || tt == 0) && nvalid > 0;
         XT xi[CPL], yo[CPL], t[CPL];
         XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
-        if (SP_EARLY_EPI && epi_lane) {
+        if (early_epi && epi_lane) {
             if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
             if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
         }
@@ -558,7 +570,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             for (int c = 0; c < CPL; ++c) rs[c] = (XT)acc[c];
         }
         if (nvalid <= 0) return;
-        if (!SP_EARLY_EPI) {
+        if (!early_epi) {
             if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
             if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
         }
@@ -620,7 +632,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
         int64_t s = s0 + rw;
-        if (SP_PREFETCH_META) {
+        if (prefetch_meta) {
             // the next slot's metadata is loaded while this slot is computed
             Meta cur{-1, 0, 0, -1};
             if (s < s1) cur = meta_of(s);
