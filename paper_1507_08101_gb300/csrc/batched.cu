@@ -83,6 +83,12 @@ struct BatchArgs {
 #define SP_BATCH_UNITS_PER_WARP 8
 #endif
 
+// load the next slot's metadata while the current slot runs (knob; off: the
+// registers it holds cost the kernel that carries every layout more than the
+// latency it hides, 418 -> 376 us on the 64-system float32 product)
+#ifndef SP_BATCH_PREFETCH
+#define SP_BATCH_PREFETCH 0
+#endif
 // unroll depth of the row loop for 4-column lanes (knob)
 #ifndef SP_BATCH_UNROLL_WIDE
 #define SP_BATCH_UNROLL_WIDE SP_UNROLL_WIDE
@@ -136,10 +142,14 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
     };
     int64_t s = u.s0 + rw;
     Meta cur{-1, 0, 0};
-    if (s < u.s1) cur = meta_of(s);
+    if (SP_BATCH_PREFETCH && s < u.s1) cur = meta_of(s);
     for (; s < u.s1; s += Rr) {
         Meta nxt{-1, 0, 0};
-        if (s + Rr < u.s1) nxt = meta_of(s + Rr);
+        if (SP_BATCH_PREFETCH) {
+            if (s + Rr < u.s1) nxt = meta_of(s + Rr);
+        } else {
+            cur = meta_of(s);
+        }
         const int64_t i = cur.i;
         if (i >= 0) {
             const int len_t = cur.len > tt ? (cur.len - tt + T - 1) >> lt : 0;
