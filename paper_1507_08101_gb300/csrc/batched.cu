@@ -20,6 +20,7 @@
 //     p = r + beta p,  q = s + beta q,  d = d + alpha p,  r = r - alpha q
 // (alpha = gamma / delta, beta = 0 on the first iteration).
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "spmv_kernel.cuh"
@@ -83,6 +84,11 @@ struct BatchArgs {
 #define SP_BATCH_UNITS_PER_WARP 8
 #endif
 
+// float32 inner CG: its two inner products accumulated in float per lane and
+// unit (knob; float64 across lanes and units either way)
+#ifndef SP_CG_PLAIN_DOTS
+#define SP_CG_PLAIN_DOTS 1
+#endif
 // load the next slot's metadata while the current slot runs (knob; off: the
 // registers it holds cost the kernel that carries every layout more than the
 // latency it hides, 418 -> 376 us on the 64-system float32 product)
@@ -104,7 +110,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
     constexpr int U = CPL >= 4 ? SP_BATCH_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
-    constexpr bool dots = DM != 0;
+    constexpr bool dots = (DM & 7) != 0;
     const int lt = u.log2_tpr;
     const int T = 1 << lt;
     const int gl = lane % G;
@@ -126,7 +132,9 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
     const uint32_t C = (uint32_t)Mp->C;
     const XT *__restrict__ xk = (const XT *)Mp->x + k0;
     const XT alpha = (XT)a.alpha, beta = (XT)a.beta;
-    DotAcc<XT> ayy[(DM & 1) ? CPL : 1], axy[(DM & 2) ? CPL : 1], axx[(DM & 4) ? CPL : 1];
+    // DM bit 3: accumulate in the vector precision (the float32 inner CG)
+    using Acc = typename std::conditional<(DM & 8) != 0, DotAccPlain<XT>, DotAcc<XT>>::type;
+    Acc ayy[(DM & 1) ? CPL : 1], axy[(DM & 2) ? CPL : 1], axx[(DM & 4) ? CPL : 1];
     // where a slot's row lives; the next slot's is loaded while this one runs
     struct Meta {
         int64_t i, off;
@@ -414,11 +422,14 @@ static void launch_batched_dm(int dm, int grid, const BatchArgs &a, cudaStream_t
         k_spmmv_batched<VT, XT, 0><<<grid, kBatchThreads, 0, s>>>(a);
     else if (dm == 6)
         k_spmmv_batched<VT, XT, 6><<<grid, kBatchThreads, 0, s>>>(a);
+    else if (dm == 14)
+        k_spmmv_batched<VT, XT, 14><<<grid, kBatchThreads, 0, s>>>(a);
     else
         k_spmmv_batched<VT, XT, 7><<<grid, kBatchThreads, 0, s>>>(a);
 }
 
-static int batch_launch(const Batch &B, uint32_t flags, double alpha, double beta, cudaStream_t s) {
+static int batch_launch(const Batch &B, uint32_t flags, double alpha, double beta, cudaStream_t s,
+                        bool plain_dots = false) {
     BatchArgs a;
     a.mats = (const BMat *)B.dmats->ptr;
     a.units = (const BUnit *)B.dunits->ptr;
@@ -432,7 +443,8 @@ static int batch_launch(const Batch &B, uint32_t flags, double alpha, double bet
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.grid, (a.nunits + kBatchWarps - 1) / kBatchWarps));
     // dot set compiled in: none, the CG pair <x,y>, <x,x>, or all three
     const int req = (int)((flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY);
-    const int dm = req == 0 ? 0 : (req & 1) ? 7 : 6;
+    int dm = req == 0 ? 0 : (req & 1) ? 7 : 6;
+    if (dm == 6 && plain_dots && B.xdt == SP_F32) dm = 14;
     if (B.vdt == SP_F64 && B.xdt == SP_F64)
         launch_batched_dm<double, double>(dm, grid, a, s);
     else if (B.vdt == SP_F32 && B.xdt == SP_F32)
@@ -832,7 +844,7 @@ int sp_cg_create(sp_cg **out, int count, sp_mat *const *A, const int32_t *widths
 
 static int cg_inner_iteration(sp_cg *cg, int f64, double inner_tol2, cudaStream_t s) {
     Batch &B = f64 ? cg->b64in : cg->b32;
-    SP_TRY(batch_launch(B, SP_SPMV_DOT_XX | SP_SPMV_DOT_XY, 1.0, 0.0, s));
+    SP_TRY(batch_launch(B, SP_SPMV_DOT_XX | SP_SPMV_DOT_XY, 1.0, 0.0, s, SP_CG_PLAIN_DOTS != 0));
     k_cg_scalars<<<cg->count, 32 * kBatchMaxW, 0, s>>>((const BMat *)B.dmats->ptr, (const double *)B.partials->ptr,
                                                        cg->count, inner_tol2, (CGCol *)cg->cgcol->ptr,
                                                        (double *)cg->coef->ptr, (float2 *)cg->coef_f->ptr);

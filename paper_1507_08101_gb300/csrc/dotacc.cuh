@@ -11,6 +11,16 @@
 
 namespace sp {
 
+// Plain accumulation in the vector precision (the float32 inner CG, whose
+// iterates need far less than float64 accuracy in their inner products; the
+// sums across lanes and units are still added in float64).
+template <class XT>
+struct DotAccPlain {
+    XT v = XT(0);
+    __device__ __forceinline__ void add(XT a, XT b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double value() const { return (double)v; }
+};
+
 template <class XT>
 struct DotAcc;
 
