@@ -53,8 +53,19 @@ def test_tuned_batch_runs_and_caches(cuda_ok, tmp_path):
     b2.bind(xs, y2)
     b2.spmv()
     torch.cuda.synchronize()
-    for a, b in zip(y1, y2):
-        assert torch.equal(a, b)
+    import oracle
+    for a, b, A, c, x in zip(y1, y2, mats, cfg, xs):
+        if c["C"] == 32:
+            # one lane per row in every layout: the same sums, bit for bit
+            assert torch.equal(a, b)
+        else:
+            # rows split over several lanes add their products in an order that
+            # depends on the lane layout: equal within the float32 bound
+            X = x.double().cpu().numpy()
+            sc = oracle.spmmv_scale(A, X, val=oracle.round_values(A.val, "f32"))
+            tol = 2 * 1.1 * (int(np.diff(A.rowptr).max()) + 6) * 2.0 ** -24
+            d = np.abs(a.double().cpu().numpy() - b.double().cpu().numpy())
+            assert np.all(d <= tol * sc + 1e-30)
 
 
 @pytest.mark.gpu
