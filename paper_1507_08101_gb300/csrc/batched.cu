@@ -198,6 +198,18 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
         cur = nxt;
     }
     if constexpr (dots) {
+        if constexpr ((DM & 8) != 0) {
+            // plain accumulators: the xor tree across lanes in the vector
+            // precision too (one conversion per unit instead of one per step)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int o = G; o < 32; o <<= 1) {
+                    if constexpr ((DM & 1) != 0) ayy[c].v += __shfl_xor_sync(0xffffffffu, ayy[c].v, o);
+                    if constexpr ((DM & 2) != 0) axy[c].v += __shfl_xor_sync(0xffffffffu, axy[c].v, o);
+                    if constexpr ((DM & 4) != 0) axx[c].v += __shfl_xor_sync(0xffffffffu, axx[c].v, o);
+                }
+        }
         double dyy[CPL], dxy[CPL], dxx[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -205,7 +217,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
             dxy[c] = (DM & 2) ? axy[(DM & 2) ? c : 0].value() : 0.0;
             dxx[c] = (DM & 4) ? axx[(DM & 4) ? c : 0].value() : 0.0;
 #pragma unroll
-            for (int o = G; o < 32; o <<= 1) {
+            for (int o = G; o < 32 && (DM & 8) == 0; o <<= 1) {
                 if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
                 if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
                 if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
