@@ -17,6 +17,11 @@ Functions and the passage of GHOST (arxiv 1507.08101) each one follows:
   application of Sec. "Introduction"); :func:`mixed_precision_cg` -- iterative
   refinement around a float32 inner solve.
 * :func:`round_values` -- float32 and bfloat16 storage rounding.
+* :func:`kpm_moments` -- Chebyshev moments mu_k = <x, T_k(A~) x> of the kernel
+  polynomial method that Sec. "Kernel fusion" names as the solver the fused
+  product serves (A. Weisse, G. Wellein, A. Alvermann and H. Fehske, "The
+  kernel polynomial method", Rev. Mod. Phys. 78 (2006)), by the definition:
+  the three-term recurrence up to k and one inner product per moment.
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense brute force, closed-form eigenpairs, format identities from the
@@ -339,3 +344,30 @@ def _spmv_f32(A, v32, p):
     """Row sums of float32 products in float32 (plain loop order of CSR rows)."""
     prod = (v32 * p[A.col]).astype(np.float32)
     return np.add.reduceat(prod, A.rowptr[:-1]).astype(np.float32) * (np.diff(A.rowptr) > 0)
+
+
+# --------------------------------------------------------------------------- KPM moments
+
+def kpm_moments(A, X, nmom: int, a: float, b: float):
+    """mu[k, c] = <x_c, T_k(A~) x_c> for k < nmom, A~ = (A - b I) / a.
+
+    The definition itself: w_0 = x, w_1 = A~ w_0, w_{k+1} = 2 A~ w_k - w_{k-1}
+    (the Chebyshev recurrence), and mu_k = <w_0, w_k>, one product per k.
+    Returns an (nmom, w) float64 array."""
+    X = np.asarray(X, np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    w0 = X.copy()
+    mu = np.empty((nmom, X.shape[1]))
+    mu[0] = (w0 * w0).sum(0)
+    if nmom == 1:
+        return mu
+    w1 = (spmmv(A, w0)[0] - b * w0) / a
+    mu[1] = (w0 * w1).sum(0)
+    prev, cur = w0, w1
+    for k in range(2, nmom):
+        nxt = 2.0 * (spmmv(A, cur)[0] - b * cur) / a - prev
+        mu[k] = (w0 * nxt).sum(0)
+        prev, cur = cur, nxt
+    return mu
+
