@@ -482,6 +482,59 @@ def secondary_powerlaw(peak):
             "bwd_us": round(bwd * 1e3, 1), "bwd_GBs": round(nb_bwd / bwd / 1e6, 1)}
 
 
+def secondary_kpm(peak):
+    """KPM moments on the Anderson 128^3 matrix with a width-16 block (the
+    solver the fused product serves): 128 moments from 64 fused products
+    (sp_kpm_moments), against the same Chebyshev loop with the products
+    unfused (sp_spmv without dots, then the two inner products as separate
+    passes over the block vectors: torch reductions, a comparison only)."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    from workloads import generators as gen
+    A, X = gen.workload_anderson()
+    a = 1.01 * (6 + 8.25)
+    nmom = 128
+    out = {"nmom": nmom, "w": 16}
+    for vdt, xdt in (("f64", "f64"), ("f32", "f32")):
+        tdt = torch.float64 if xdt == "f64" else torch.float32
+        m = sellcs.SellMatrix(A, C=32, sigma=1, dtype=vdt)
+        x = torch.from_numpy(X).to("cuda", tdt)
+        sellcs.kpm_moments(m, x, nmom, a, 0.0)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            mu = sellcs.kpm_moments(m, x, nmom, a, 0.0)
+        fused = (time.perf_counter() - t0) / reps
+
+        def unfused():
+            u = x.clone()
+            v = torch.empty_like(u)
+            mu0 = (u * u).sum(0)
+            sellcs.spmv(m, u, v, alpha=1 / a)
+            mus = [mu0, (u * v).sum(0)]
+            for n in range(1, nmom // 2):
+                sellcs.spmv(m, v, u, alpha=2 / a, beta=-1.0)
+                mus.append(2 * (v * v).sum(0) - mu0)  # mu_{2n}
+                mus.append(2 * (u * v).sum(0) - mus[1])  # mu_{2n+1}
+                u, v = v, u
+            return torch.stack(mus[:nmom]).cpu()
+
+        unfused()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mu_u = unfused()
+        torch.cuda.synchronize()
+        unf = (time.perf_counter() - t0) / reps
+        rel = float(np.max(np.abs(mu - mu_u.double().numpy()) / np.abs(mu[0])))
+        out[f"{vdt}_vals_{xdt}_vecs"] = {"fused_ms": round(fused * 1e3, 2), "per_product_us": round(fused / (nmom // 2) * 1e6, 1),
+                                         "unfused_ms": round(unf * 1e3, 2), "speedup_fused": round(unf / fused, 2),
+                                         "max_rel_diff_fused_vs_unfused": rel}
+        m.close()
+    return out
+
+
 def secondary_cg_batch(peak):
     """64 SPD systems L_2D(s) + 0.01 I, s in [64, 512], widths 1..8.
     (a) one persistent batched f32 SpMMV launch vs one batched f64 launch vs 64
@@ -622,7 +675,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch"],
+    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm"],
                     help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -639,7 +692,7 @@ def main():
         from paper_1507_08101_gb300 import build
         build.build()
         fns = {"laplace": secondary_laplace, "anderson_w16": secondary_anderson,
-               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch}
+               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
         return
     if world > 1:
@@ -658,7 +711,8 @@ def main():
         peak = result["roofline"]["peak"]
         sec = {}
         for name, fn in (("laplace", secondary_laplace), ("anderson_w16", secondary_anderson),
-                         ("powerlaw_adjoint", secondary_powerlaw), ("cg_batch", secondary_cg_batch)):
+                         ("powerlaw_adjoint", secondary_powerlaw), ("cg_batch", secondary_cg_batch),
+                         ("kpm", secondary_kpm)):
             try:
                 sec[name] = fn(peak)
             except Exception as e:  # a failed secondary measurement must not hide the headline

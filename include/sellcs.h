@@ -231,6 +231,27 @@ SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spm
 SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
                     void *stream);
 
+/* ------------------------------------------------------------------ KPM moments */
+
+/*
+ * Chebyshev moments of the kernel polynomial method, the solver Sec. "Kernel
+ * fusion" names as the user of the fused product: with A~ = (A - b I) / a,
+ *     mu[k * w + c] = < x_c, T_k(A~) x_c >,   k = 0 .. nmom-1, c = 0 .. w-1.
+ * Each Chebyshev step w_{n+1} = 2 A~ w_n - w_{n-1} is one sp_spmv (SCALE,
+ * SHIFT, AXPBY with beta = -1) whose fused <y,y> and <x,y> give two moments
+ * (mu_{2n} = 2 <w_n,w_n> - mu_0, mu_{2n+1} = 2 <w_{n+1},w_n> - mu_1), so
+ * about nmom / 2 products.
+ *   A      square matrix
+ *   x      start block, nrows x w, row-major, device (read only)
+ *   nmom   number of moments, >= 1
+ *   a, b   scaling (a != 0, both finite); the spectrum of A should map into
+ *          [-1, 1] for the moments to stay bounded
+ *   mu     host array of nmom * w doubles, written
+ * Allocates two nrows x w work blocks for the call; synchronises the stream.
+ */
+SP_API int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, double b, double *mu,
+                          void *stream);
+
 /* ------------------------------------------------------------------ host block vectors */
 
 /*

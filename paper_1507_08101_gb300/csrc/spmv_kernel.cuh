@@ -27,6 +27,7 @@
 // result is deterministic and no block ever waits for another.
 #pragma once
 
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string.h>
@@ -394,7 +395,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
 
 // Final step of the fused reductions: per-block partial sums, and the last
 // block to arrive adds them up in block order.
-template <int CPL, int G>
+template <int CPL, int G, int DM>
 __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&dyy)[CPL], double (&dxy)[CPL],
                                             double (&dxx)[CPL]) {
     __shared__ double sred[kMainWarps][3][kMaxTileW];
@@ -404,9 +405,9 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
     for (int c = 0; c < CPL; ++c) {
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
-            dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
-            dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
-            dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
+            if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
+            if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
+            if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
         }
     }
     if (lane < G) {
@@ -476,10 +477,18 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool LS>
+// DM: the dot products compiled in (bit 0 <y,y>, bit 1 <x,y>, bit 2 <x,x>);
+// the launcher uses 0, 3 (the pair of the bench product and of the KPM steps)
+// or 7, and the flags pick which of them are written.
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
+    // dot accumulators per lane: float64 for float64 vectors; for float32
+    // vectors float per lane (a few tens of rows each), float64 from the
+    // warp reduction on, so the kernel spends no float64 instruction per row
+    using DT = typename std::conditional<sizeof(XT) == 8, double, float>::type;
+    constexpr bool DOTS = DM != 0;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
@@ -509,9 +518,13 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
 #pragma unroll
     for (int c = 0; c < CPL; ++c) gam[c] = (shift && k0 + c < a.w) ? (XT)a.gamma[k0 + c] : XT(0);
 
-    double dyy[CPL], dxy[CPL], dxx[CPL];
+    DT dyy[(DM & 1) ? CPL : 1], dxy[(DM & 2) ? CPL : 1], dxx[(DM & 4) ? CPL : 1];
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) dyy[c] = dxy[c] = dxx[c] = 0.0;
+    for (int c = 0; c < CPL; ++c) {
+        if constexpr ((DM & 1) != 0) dyy[c] = DT(0);
+        if constexpr ((DM & 2) != 0) dxy[c] = DT(0);
+        if constexpr ((DM & 4) != 0) dxx[c] = DT(0);
+    }
 
     const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
 
@@ -587,10 +600,13 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 if (c < nvalid) {
-                    double td = (double)t[c], xd = need_xi ? (double)xi[c] : 0.0;
-                    if (f & SP_SPMV_DOT_YY) dyy[c] = fma_rn(td, td, dyy[c]);
-                    if (f & SP_SPMV_DOT_XY) dxy[c] = fma_rn(xd, td, dxy[c]);
-                    if (f & SP_SPMV_DOT_XX) dxx[c] = fma_rn(xd, xd, dxx[c]);
+                    const DT td = (DT)t[c], xd = need_xi ? (DT)xi[c] : DT(0);
+                    if constexpr ((DM & 1) != 0)
+                        if (f & SP_SPMV_DOT_YY) dyy[c] = fma_rn(td, td, dyy[c]);
+                    if constexpr ((DM & 2) != 0)
+                        if (f & SP_SPMV_DOT_XY) dxy[c] = fma_rn(xd, td, dxy[c]);
+                    if constexpr ((DM & 4) != 0)
+                        if (f & SP_SPMV_DOT_XX) dxx[c] = fma_rn(xd, xd, dxx[c]);
                 }
             }
         }
@@ -652,7 +668,16 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             if (s < a.nslots) slot(meta_of(s));
         }
     }
-    if constexpr (DOTS) reduce_dots<CPL, G>(a, k0, dyy, dxy, dxx);
+    if constexpr (DOTS) {
+        double vyy[CPL], vxy[CPL], vxx[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            vyy[c] = (DM & 1) ? (double)dyy[(DM & 1) ? c : 0] : 0.0;
+            vxy[c] = (DM & 2) ? (double)dxy[(DM & 2) ? c : 0] : 0.0;
+            vxx[c] = (DM & 4) ? (double)dxx[(DM & 4) ? c : 0] : 0.0;
+        }
+        reduce_dots<CPL, G, DM>(a, k0, vyy, vxy, vxx);
+    }
 }
 
 // Host-side dispatch over the block width for one (value, vector) type pair.

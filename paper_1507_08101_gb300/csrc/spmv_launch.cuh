@@ -32,7 +32,7 @@ namespace sp {
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, bool DOTS, bool MT, bool LS>
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
@@ -40,9 +40,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DM, MT, LS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DM, MT, LS>,
                                                                       kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -75,19 +75,23 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     }
     b.nsm = sms;
     b.log2_tpr = lt;
-    k_spmmv<VT, XT, WP, VEC, DOTS, MT, LS><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
+    k_spmmv<VT, XT, WP, VEC, DM, MT, LS><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
 template <class VT, class XT, int WP, bool MT, bool LS>
 static int launch_spmv_wml(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
-    const bool dots = (a.flags & SP_SPMV_DOT_ANY) != 0;
-    if (dots)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, true, MT, LS>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, true, MT, LS>(a, max_blocks, s);
-    return vec ? launch_spmv_variant<VT, XT, WP, true, false, MT, LS>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false, false, MT, LS>(a, max_blocks, s);
+    // dot set compiled in: none, <y,y> and <x,y>, or all three
+    const uint32_t req = (a.flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY;
+    if (req & 4)
+        return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS>(a, max_blocks, s);
+    if (req)
+        return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS>(a, max_blocks, s);
+    return vec ? launch_spmv_variant<VT, XT, WP, true, 0, MT, LS>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, 0, MT, LS>(a, max_blocks, s);
 }
 
 // Lockstep row loop (row_product_ls) or per-lane loop: the lockstep form saves

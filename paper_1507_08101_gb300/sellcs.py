@@ -108,6 +108,7 @@ _SIGS = {
     "sp_cg_destroy": (I, [P, P]),
     "sp_spmv_noalloc": (I, [P, I, P, P, P, P, I64, I64, I32, P, I64, P, I64, P, I64, I32, I, ct.c_uint32,
                             ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.c_double, ct.c_double, P, P]),
+    "sp_kpm_moments": (I, [P, P, I32, ct.c_double, ct.c_double, P, P]),
     "sp_host_plan_create": (I, [PP, P, I32, I]),
     "sp_spmv_host": (I, [P, P, P, P, P, P, P, ct.POINTER(sp_spmv_opts)]),
     "sp_host_plan_sync": (I, [P]),
@@ -405,6 +406,21 @@ def spmv(A: SellMatrix, x, y, *, alpha=None, gamma=None, beta=None, dot_yy=False
         if hz is not None:
             L.sp_dense_destroy(hz, None)
     return dot
+
+
+def kpm_moments(A: SellMatrix, x, nmom: int, a: float, b: float, stream=None) -> np.ndarray:
+    """Chebyshev moments mu[k, c] = <x_c, T_k((A - b I) / a) x_c> (sp_kpm_moments);
+    x: CUDA tensor (n,) or (n, w), row-major.  Returns an (nmom, w) array."""
+    L = lib()
+    w = 1 if x.dim() == 1 else x.shape[1]
+    hx = sp_dense_view(x)
+    mu = np.empty((int(nmom), w), np.float64)
+    try:
+        check(L.sp_kpm_moments(A.handle, hx, int(nmom), float(a), float(b), ct.c_void_p(mu.ctypes.data),
+                               _stream(stream)), "sp_kpm_moments")
+    finally:
+        L.sp_dense_destroy(hx, None)
+    return mu
 
 
 def _host_ptr(a):

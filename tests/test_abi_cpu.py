@@ -56,6 +56,7 @@ def test_host_argument_checks(L):
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 7, 0, None) == s.SP_ERR_DTYPE
     assert L.sp_mat_create_csr(ct.byref(h), -1, 1, rp, None, None, 32, 1, 0, 0, None) == s.SP_ERR_DIM
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 0, 1 << 9, None) == s.SP_ERR_ARG
+    assert L.sp_kpm_moments(None, None, 4, 1.0, 0.0, None, None) == s.SP_ERR_ARG
     assert L.sp_host_plan_create(None, None, 1, s.SP_F64) == s.SP_ERR_ARG
     assert L.sp_spmv_host(None, None, None, None, None, None, None, None) == s.SP_ERR_ARG
     assert L.sp_host_plan_sync(None) == s.SP_ERR_ARG
