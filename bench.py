@@ -482,6 +482,38 @@ def secondary_powerlaw(peak):
             "bwd_us": round(bwd * 1e3, 1), "bwd_GBs": round(nb_bwd / bwd / 1e6, 1)}
 
 
+def secondary_permuted(peak):
+    """The bench product (irregular N = 2^21, SELL-32-256, augmented) with the
+    vectors in SELL row order (SP_MAT_PERMUTED_SPACE): same algorithmic bytes,
+    x_i, y and z accessed at consecutive rows of a chunk."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    A, X, Y0, Z0 = make_workload()
+    W = WORKLOAD
+    out = {}
+    for name, perm in (("user_order", False), ("sell_order", True)):
+        m = sellcs.SellMatrix(A, C=W["C"], sigma=W["sigma"], dtype="f64", permuted=perm)
+        inf = m.info()
+        x, y, z = (torch.from_numpy(v).cuda() for v in (X, Y0, Z0))
+        if perm:
+            xp, yp, zp = torch.empty_like(x), torch.empty_like(y), torch.empty_like(z)
+            for src, dst in ((x, xp), (y, yp), (z, zp)):
+                sellcs.mat_permute(m, dst, src, True)
+            x, y, z = xp, yp, zp
+        dot = torch.zeros(3, dtype=torch.float64, device="cuda")
+        kw = dict(alpha=W["alpha"], gamma=W["gamma"], beta=W["beta"], dot_xy=True, dot_yy=True, z=z,
+                  delta=W["delta"], eta=W["eta"], dot=dot)
+        for _ in range(5):
+            sellcs.spmv(m, x, y, **kw)
+        torch.cuda.synchronize()
+        ms = _events_time(lambda: sellcs.spmv(m, x, y, **kw), 200, torch.cuda.current_stream())
+        nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * W["C"], 1, 8, 8, True, True,
+                               W["sigma"] > 1)
+        out[name] = {"us": round(ms * 1e3, 1), "GBs": round(nb / ms / 1e6, 1), "frac_of_peak": round(nb / ms / 1e6 / peak, 4)}
+        m.close()
+    return out
+
+
 def secondary_kpm(peak):
     """KPM moments on the Anderson 128^3 matrix with a width-16 block (the
     solver the fused product serves): 128 moments from 64 fused products
@@ -675,7 +707,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm"],
+    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm", "permuted"],
                     help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -692,7 +724,8 @@ def main():
         from paper_1507_08101_gb300 import build
         build.build()
         fns = {"laplace": secondary_laplace, "anderson_w16": secondary_anderson,
-               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm}
+               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
+               "permuted": secondary_permuted}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
         return
     if world > 1:

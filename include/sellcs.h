@@ -82,6 +82,14 @@ typedef struct sp_dense sp_dense; /* opaque: dense block vector (owning or view)
  * The order changes only which warp computes which row, never a result. */
 #define SP_MAT_ORDER_FRONT (1u << 3)  /* moving front: all warps work on one run of rows at a time */
 #define SP_MAT_ORDER_RANGES (1u << 4) /* each warp owns one contiguous cost-balanced range of rows */
+/* Vectors in SELL row order (GHOST's permuted space; nrows == ncols): the
+ * column indices are stored as slots (col' = the slot of row col), so x, y
+ * and z of every product are indexed by slot: row s of them is user row
+ * perm[s] (sp_mat_permute moves block vectors between the two orders).  The
+ * products read x and write y, z at consecutive rows of a chunk.  Not with
+ * SP_MAT_WITH_TRANSPOSE.  sp_mat_export_sell returns the stored (slot)
+ * indices; sp_mat_to_csr returns the user's CSR. */
+#define SP_MAT_PERMUTED_SPACE (1u << 5)
 
 /*
  * Build a SELL-C-sigma matrix from CSR (GHOST: "construct a SELL-C-sigma matrix
@@ -230,6 +238,16 @@ SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spm
  */
 SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
                     void *stream);
+
+/*
+ * Block vector between the user's row order and the SELL row order of A:
+ *   to_sell != 0:  out[s, :] = in[perm[s], :]   for s < nrows
+ *   to_sell == 0:  out[perm[s], :] = in[s, :]
+ * (perm = the row permutation of A; the identity when sigma = 1).  in and out:
+ * nrows x w device blocks of the same dtype, row-major, not overlapping.
+ * Asynchronous on the stream.
+ */
+SP_API int sp_mat_permute(const sp_mat *A, sp_dense *out, const sp_dense *in, int to_sell, void *stream);
 
 /* ------------------------------------------------------------------ KPM moments */
 

@@ -78,7 +78,7 @@ int launch_spmv(const SpmvLaunch &L, cudaStream_t s) {
     a.chunkptr = (const int64_t *)P.chunkptr->ptr;
     a.chunklen = (const int32_t *)P.chunklen->ptr;
     a.slotlen = (const int32_t *)P.slotlen->ptr;
-    a.perm = P.sigma == 1 ? nullptr : (const int32_t *)P.perm->ptr;
+    a.perm = (P.sigma == 1 || P.permuted_space) ? nullptr : (const int32_t *)P.perm->ptr;
     a.nrows = P.nrows;
     a.nslots = P.nslots;
     a.C = P.C;
@@ -199,9 +199,11 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     if (C < 1 || C > 1024 || sigma < 1) return SP_ERR_ARG;
     if (!valid_val_dtype(val_dtype)) return SP_ERR_DTYPE;
     if (flags & ~(SP_MAT_CSR_ON_DEVICE | SP_MAT_VAL_F32 | SP_MAT_WITH_TRANSPOSE | SP_MAT_ORDER_FRONT |
-                  SP_MAT_ORDER_RANGES))
+                  SP_MAT_ORDER_RANGES | SP_MAT_PERMUTED_SPACE))
         return SP_ERR_ARG;
     if ((flags & SP_MAT_ORDER_FRONT) && (flags & SP_MAT_ORDER_RANGES)) return SP_ERR_ARG;
+    if ((flags & SP_MAT_PERMUTED_SPACE) && (flags & SP_MAT_WITH_TRANSPOSE)) return SP_ERR_ARG;
+    if ((flags & SP_MAT_PERMUTED_SPACE) && nrows != ncols) return SP_ERR_DIM;
     cudaStream_t s = (cudaStream_t)stream;
     bool on_dev = flags & SP_MAT_CSR_ON_DEVICE;
     bool f32 = flags & SP_MAT_VAL_F32;
@@ -234,7 +236,8 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     }
     sp_mat *A = new sp_mat();
     A->vdt = val_dtype;
-    int rc = build_pattern_and_values(A, nrows, ncols, prp, pcol, pval, f32, C, sigma, s);
+    int rc = build_pattern_and_values(A, nrows, ncols, prp, pcol, pval, f32, C, sigma, s,
+                                      (flags & SP_MAT_PERMUTED_SPACE) != 0);
     if (rc == SP_OK && (flags & SP_MAT_WITH_TRANSPOSE)) rc = build_transpose(A, prp, pcol, pval, f32, s);
     if (rc == SP_OK) {
         const int order = (flags & SP_MAT_ORDER_FRONT) ? 1 : (flags & SP_MAT_ORDER_RANGES) ? 2 : 0;
@@ -375,10 +378,12 @@ int sp_mat_export_sell_transpose(const sp_mat *A, int64_t *chunkptr, int32_t *ch
 
 namespace sp {
 // SELL -> CSR on the device (inverse of the scatter).
+// colmap (may be null): map from stored indices back to the user's columns
 __global__ void k_sell_to_csr(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ perm,
                               const int32_t *__restrict__ slotlen, const int64_t *__restrict__ chunkptr,
                               const int32_t *__restrict__ col_sell, const double *__restrict__ val_sell,
-                              int64_t nslots, int C, int32_t *__restrict__ col, double *__restrict__ val) {
+                              int64_t nslots, int C, const int32_t *__restrict__ colmap, int32_t *__restrict__ col,
+                              double *__restrict__ val) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
          s += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = perm[s];
@@ -386,7 +391,8 @@ __global__ void k_sell_to_csr(const int64_t *__restrict__ rowptr, const int32_t 
         int64_t c = s / C, r = s - c * C;
         int64_t src = chunkptr[c] + r, dst = rowptr[i];
         for (int32_t j = 0; j < slotlen[s]; ++j) {
-            col[dst + j] = col_sell[src + (int64_t)j * C];
+            const int32_t cs = col_sell[src + (int64_t)j * C];
+            col[dst + j] = colmap ? colmap[cs] : cs;
             val[dst + j] = val_sell[src + (int64_t)j * C];
         }
     }
@@ -411,7 +417,9 @@ int sp_mat_to_csr(const sp_mat *A, int64_t *rowptr, int32_t *col, double *val, v
         k_sell_to_csr<<<std::max(g, 1), 256, 0, s>>>((const int64_t *)P.rowptr->ptr, (const int32_t *)P.perm->ptr,
                                                      (const int32_t *)P.slotlen->ptr,
                                                      (const int64_t *)P.chunkptr->ptr, (const int32_t *)P.col->ptr,
-                                                     (const double *)wv->ptr, P.nslots, P.C, (int32_t *)dc->ptr,
+                                                     (const double *)wv->ptr, P.nslots, P.C,
+                                                     P.permuted_space ? (const int32_t *)P.perm->ptr : nullptr,
+                                                     (int32_t *)dc->ptr,
                                                      (double *)dv->ptr);
         SP_CUDA(cudaGetLastError());
         SP_CUDA(cudaMemcpyAsync(col, dc->ptr, P.nnz * 4, cudaMemcpyDeviceToHost, s));
@@ -599,6 +607,7 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
 
 int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,
                     void *stream) {
+    if (A && A->pat->permuted_space) return SP_ERR_ARG;  // the adjoint works in the user's order
     if (!A || !g) return SP_ERR_ARG;
     const Pattern &P = *A->pat;
     cudaStream_t s = (cudaStream_t)stream;
@@ -623,3 +632,47 @@ int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *
 }
 
 }  // extern "C"
+
+namespace sp {
+// row permutation of a block vector between the user's and the SELL row order
+template <class T>
+__global__ void k_permute_rows(const int32_t *__restrict__ perm, int64_t nrows, int w, const T *__restrict__ in,
+                               int64_t ldi, T *__restrict__ out, int64_t ldo, int to_sell) {
+    const int64_t total = nrows * w;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = t / w;
+        const int k = (int)(t - s * w);
+        const int64_t i = perm[s];
+        if (to_sell)
+            out[s * ldo + k] = in[i * ldi + k];
+        else
+            out[i * ldo + k] = in[s * ldi + k];
+    }
+}
+}  // namespace sp
+
+extern "C" int sp_mat_permute(const sp_mat *A, sp_dense *out, const sp_dense *in, int to_sell, void *stream) {
+    if (!A || !out || !in) return SP_ERR_ARG;
+    const sp::Pattern &P = *A->pat;
+    if (in->nrows != P.nrows || out->nrows != P.nrows || in->ncols != out->ncols) return SP_ERR_DIM;
+    if (in->dtype != out->dtype || (in->dtype != SP_F64 && in->dtype != SP_F32)) return SP_ERR_DTYPE;
+    if (in->layout != SP_ROW_MAJOR || out->layout != SP_ROW_MAJOR) return SP_ERR_ARG;
+    const size_t xs = in->dtype == SP_F64 ? 8 : 4;
+    const char *ib = (const char *)in->ptr, *ob = (const char *)out->ptr;
+    const size_t ispan = (size_t)in->ld * in->nrows * xs, ospan = (size_t)out->ld * out->nrows * xs;
+    if (ib < ob + ospan && ob < ib + ispan) return SP_ERR_ARG;  // overlap
+    const int64_t total = P.nrows * (int64_t)in->ncols;
+    if (total == 0) return SP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 65535 * 16);
+    const int32_t *perm = (const int32_t *)P.perm->ptr;
+    if (in->dtype == SP_F64)
+        sp::k_permute_rows<double><<<grid, 256, 0, s>>>(perm, P.nrows, in->ncols, (const double *)in->ptr, in->ld,
+                                                         (double *)out->ptr, out->ld, to_sell);
+    else
+        sp::k_permute_rows<float><<<grid, 256, 0, s>>>(perm, P.nrows, in->ncols, (const float *)in->ptr, in->ld,
+                                                        (float *)out->ptr, out->ld, to_sell);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}

@@ -388,7 +388,7 @@ static int batch_init(Batch &B, int count, sp_mat *const *A, const int32_t *widt
         M.col = (const int32_t *)P.col->ptr;
         M.chunkptr = (const int64_t *)P.chunkptr->ptr;
         M.slotlen = (const int32_t *)P.slotlen->ptr;
-        M.perm = P.sigma == 1 ? nullptr : (const int32_t *)P.perm->ptr;
+        M.perm = (P.sigma == 1 || P.permuted_space) ? nullptr : (const int32_t *)P.perm->ptr;
         M.nrows = P.nrows;
         M.C = P.C;
         M.w = w;

@@ -74,6 +74,9 @@ struct Pattern {
     // (longest - shortest real row) / sum of the longest
     double lane_spread = 0.0;
     int order = 0;  // work order of the product: 0 by the size of x, 1 moving front, 2 contiguous ranges
+    // vectors in SELL row order: column indices stored as slots (col' = slot of
+    // row col), so the products read x and write y at the slot index
+    bool permuted_space = false;
 };
 using PatternPtr = std::shared_ptr<Pattern>;
 
@@ -112,7 +115,7 @@ inline int ilog2_exact(int64_t v) {
 // ------------------------------------------------------------------ conversion entry points
 int build_pattern_and_values(sp_mat *A, int64_t nrows, int64_t ncols, const int64_t *d_rowptr,
                              const int32_t *d_col, const void *d_val, bool val_f32, int C,
-                             int64_t sigma, cudaStream_t s);
+                             int64_t sigma, cudaStream_t s, bool permuted = false);
 int build_transpose(sp_mat *A, const int64_t *d_rowptr, const int32_t *d_col, const void *d_val,
                     bool val_f32, cudaStream_t s);
 int fill_values_from_csr(const Pattern &P, sp_dtype vdt, void *val_sell, const void *d_val_csr,

@@ -295,10 +295,12 @@ static int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream
 // Slot s = c*C + r holds original row perm[s]; its entry j goes to
 // chunkptr[c] + j*C + r.  Padding: column of the row's last entry (0 for an
 // empty or padding row); values are written by k_fill_values.
+// colmap (may be null): column index map applied to every stored index (the
+// slot of each row, for matrices whose vectors live in SELL row order)
 __global__ void k_scatter_cols(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                const int32_t *__restrict__ perm, const int32_t *__restrict__ chunklen,
                                const int64_t *__restrict__ chunkptr, int64_t nslots, int C,
-                               int32_t *__restrict__ col_sell) {
+                               const int32_t *__restrict__ colmap, int32_t *__restrict__ col_sell) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
          s += (int64_t)gridDim.x * blockDim.x) {
         int64_t c = s / C;
@@ -309,8 +311,20 @@ __global__ void k_scatter_cols(const int64_t *__restrict__ rowptr, const int32_t
         int32_t pad = len > 0 ? col[start + len - 1] : 0;
         int64_t base = chunkptr[c] + r;
         int32_t cl = chunklen[c];
-        for (int64_t j = 0; j < cl; ++j) col_sell[base + j * C] = j < len ? col[start + j] : pad;
+        if (colmap && len > 0) pad = colmap[pad];
+        for (int64_t j = 0; j < cl; ++j) {
+            int32_t v = pad;
+            if (j < len) v = colmap ? colmap[col[start + j]] : col[start + j];
+            col_sell[base + j * C] = v;
+        }
     }
+}
+
+// inv[perm[s]] = s for the real slots (s < nrows)
+__global__ void k_invert_perm(const int32_t *__restrict__ perm, int64_t nrows, int32_t *__restrict__ inv) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nrows;
+         s += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[s]] = (int32_t)s;
 }
 
 template <class S, class D>
@@ -541,7 +555,7 @@ int build_partition(Pattern &P, cudaStream_t s) {
 
 int build_pattern_and_values(sp_mat *A, int64_t N, int64_t ncols, const int64_t *d_rowptr,
                              const int32_t *d_col, const void *d_val, bool val_f32, int C,
-                             int64_t sigma, cudaStream_t s) {
+                             int64_t sigma, cudaStream_t s, bool permuted) {
     auto P = std::make_shared<Pattern>();
     P->nrows = N;
     P->ncols = ncols;
@@ -623,11 +637,22 @@ int build_pattern_and_values(sp_mat *A, int64_t N, int64_t ncols, const int64_t 
     // 4. scatter
     SP_TRY(dev_alloc(P->col, nstored * sizeof(int32_t), s));
     if (P->nslots > 0) {
+        Tmp inv(s);
+        const int32_t *colmap = nullptr;
+        if (permuted) {
+            SP_TRY(inv.alloc(std::max<int64_t>(N, 1) * sizeof(int32_t)));
+            k_invert_perm<<<grid_for(std::max<int64_t>(N, 1)), kThreads, 0, s>>>((const int32_t *)P->perm->ptr, N,
+                                                                              inv.as<int32_t>());
+            SP_CUDA(cudaGetLastError());
+            colmap = inv.as<int32_t>();
+        }
         k_scatter_cols<<<grid_for(P->nslots), kThreads, 0, s>>>(
             d_rowptr, d_col, (const int32_t *)P->perm->ptr, (const int32_t *)P->chunklen->ptr,
-            (const int64_t *)P->chunkptr->ptr, P->nslots, C, (int32_t *)P->col->ptr);
+            (const int64_t *)P->chunkptr->ptr, P->nslots, C, colmap, (int32_t *)P->col->ptr);
         SP_CUDA(cudaGetLastError());
+        SP_CUDA(cudaStreamSynchronize(s));
     }
+    P->permuted_space = permuted;
     SP_TRY(build_partition(*P, s));
     DevBufPtr val;
     SP_TRY(dev_alloc(val, nstored * dtype_size(A->vdt), s));

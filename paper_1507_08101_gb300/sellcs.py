@@ -24,6 +24,7 @@ SP_F64, SP_F32, SP_BF16 = 0, 1, 2
 SP_ROW_MAJOR, SP_COL_MAJOR = 0, 1
 SP_MAT_CSR_ON_DEVICE, SP_MAT_VAL_F32, SP_MAT_WITH_TRANSPOSE = 1, 2, 4
 SP_MAT_ORDER_FRONT, SP_MAT_ORDER_RANGES = 8, 16
+SP_MAT_PERMUTED_SPACE = 32
 ORDERS = {"auto": 0, "front": SP_MAT_ORDER_FRONT, "ranges": SP_MAT_ORDER_RANGES}
 SP_SPMV_SCALE = 1 << 0
 SP_SPMV_SHIFT = 1 << 1
@@ -109,6 +110,7 @@ _SIGS = {
     "sp_spmv_noalloc": (I, [P, I, P, P, P, P, I64, I64, I32, P, I64, P, I64, P, I64, I32, I, ct.c_uint32,
                             ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.c_double, ct.c_double, P, P]),
     "sp_kpm_moments": (I, [P, P, I32, ct.c_double, ct.c_double, P, P]),
+    "sp_mat_permute": (I, [P, P, P, I, P]),
     "sp_host_plan_create": (I, [PP, P, I32, I]),
     "sp_spmv_host": (I, [P, P, P, P, P, P, P, ct.POINTER(sp_spmv_opts)]),
     "sp_host_plan_sync": (I, [P]),
@@ -224,10 +226,13 @@ class SellMatrix:
     a tuple (nrows, ncols, rowptr, col, val) of CUDA tensors (then the CSR is
     read on the device)."""
 
-    def __init__(self, csr, C=32, sigma=1, dtype="f64", with_transpose=False, stream=None, order="auto"):
+    def __init__(self, csr, C=32, sigma=1, dtype="f64", with_transpose=False, stream=None, order="auto",
+                 permuted=False):
         import torch
         self._lib = lib()
         flags = (SP_MAT_WITH_TRANSPOSE if with_transpose else 0) | ORDERS[order]
+        if permuted:
+            flags |= SP_MAT_PERMUTED_SPACE
         if isinstance(csr, tuple):
             nrows, ncols, rowptr, col, val = csr
             flags |= SP_MAT_CSR_ON_DEVICE
@@ -406,6 +411,19 @@ def spmv(A: SellMatrix, x, y, *, alpha=None, gamma=None, beta=None, dot_yy=False
         if hz is not None:
             L.sp_dense_destroy(hz, None)
     return dot
+
+
+def mat_permute(A: SellMatrix, out, inp, to_sell: bool, stream=None):
+    """out = inp in A's SELL row order (to_sell) or back in the user's order
+    (sp_mat_permute); CUDA tensors (n,) or (n, w), row-major."""
+    L = lib()
+    ho, hi = sp_dense_view(out), sp_dense_view(inp)
+    try:
+        check(L.sp_mat_permute(A.handle, ho, hi, 1 if to_sell else 0, _stream(stream)), "sp_mat_permute")
+    finally:
+        L.sp_dense_destroy(ho, None)
+        L.sp_dense_destroy(hi, None)
+    return out
 
 
 def kpm_moments(A: SellMatrix, x, nmom: int, a: float, b: float, stream=None) -> np.ndarray:
