@@ -82,7 +82,8 @@ typedef struct sp_dense sp_dense; /* opaque: dense block vector (owning or view)
  * The order changes only which warp computes which row, never a result. */
 #define SP_MAT_ORDER_FRONT (1u << 3)  /* moving front: all warps work on one run of rows at a time */
 #define SP_MAT_ORDER_RANGES (1u << 4) /* each warp owns one contiguous cost-balanced range of rows */
-/* Vectors in SELL row order (GHOST's permuted space; nrows == ncols): the
+/* Vectors in SELL row order (the local permutation of GHOST's sparse-matrix
+ * section applied to rows and columns alike; nrows == ncols): the
  * column indices are stored as slots (col' = the slot of row col), so x, y
  * and z of every product are indexed by slot: row s of them is user row
  * perm[s] (sp_mat_permute moves block vectors between the two orders).  The
