@@ -514,6 +514,36 @@ def secondary_permuted(peak):
     return out
 
 
+def secondary_tsm(peak):
+    """Tall and skinny kernels on n = 2^22 rows, m = k = 16: V^T W (plain and
+    Kahan) and V X.  Bytes: V and W read once (tsmttsm); V read, W written
+    (tsmm, beta = 0); flops 2 n m k."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    n, m, k = 1 << 22, 16, 16
+    out = {"n": n, "m": m, "k": k}
+    for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        g = torch.Generator(device="cuda").manual_seed(5)
+        V = torch.rand(n, m, dtype=tdt, device="cuda", generator=g)
+        W = torch.rand(n, k, dtype=tdt, device="cuda", generator=g)
+        X = torch.zeros(m, k, dtype=tdt, device="cuda")
+        S = torch.rand(m, k, dtype=tdt, device="cuda", generator=g)
+        es = V.element_size()
+        res = {}
+        for name, fn, nbytes in (
+                ("tsmttsm", lambda: sellcs.tsmttsm(X, V, W, 1.0, 0.0, False), n * (m + k) * es),
+                ("tsmttsm_kahan", lambda: sellcs.tsmttsm(X, V, W, 1.0, 0.0, True), n * (m + k) * es),
+                ("tsmm", lambda: sellcs.tsmm(W, V, S, 1.0, 0.0), n * (m + k) * es)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ms = _events_time(fn, 20, torch.cuda.current_stream())
+            res[name] = {"us": round(ms * 1e3, 1), "GBs": round(nbytes / ms / 1e6, 1),
+                         "TFLOPs": round(2.0 * n * m * k / ms / 1e9, 3)}
+        out[dt] = res
+    return out
+
+
 def secondary_kpm(peak):
     """KPM moments on the Anderson 128^3 matrix with a width-16 block (the
     solver the fused product serves): 128 moments from 64 fused products
@@ -707,7 +737,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm", "permuted"],
+    ap.add_argument("--only", choices=["laplace", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm", "permuted", "tsm"],
                     help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -725,7 +755,7 @@ def main():
         build.build()
         fns = {"laplace": secondary_laplace, "anderson_w16": secondary_anderson,
                "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
-               "permuted": secondary_permuted}
+               "permuted": secondary_permuted, "tsm": secondary_tsm}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
         return
     if world > 1:

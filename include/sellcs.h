@@ -250,6 +250,26 @@ SP_API int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_
  */
 SP_API int sp_mat_permute(const sp_mat *A, sp_dense *out, const sp_dense *in, int to_sell, void *stream);
 
+/* ------------------------------------------------------------------ tall and skinny kernels */
+
+/*
+ * The tall and skinny block-vector kernels of the dense-matrix section of the
+ * paper (ghost_tsmttsm, ghost_tsmm, ghost_tsmm_inplace), with V n x m,
+ * W n x k (m, k <= 32 << n) and the small X m x k, all row-major device
+ * blocks of one dtype (SP_F64 or SP_F32):
+ *   sp_tsmttsm   X <- alpha V^T W + beta X   (kahan != 0: Kahan-compensated
+ *                sums, the variant the paper adds for large n).  The result
+ *                does not depend on timing (per-block sums added in block
+ *                order).  beta = 0: X is not read.
+ *   sp_tsmm      W <- alpha V X + beta W; W may be V itself (in place, then
+ *                k = m); any other overlap of W with V or X is SP_ERR_ARG.
+ *                beta = 0: W is not read.
+ * SP_ERR_UNSUPPORTED for m or k above 32.  Asynchronous on the stream.
+ */
+SP_API int sp_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, double beta, int kahan,
+                      void *stream);
+SP_API int sp_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, double beta, void *stream);
+
 /* ------------------------------------------------------------------ KPM moments */
 
 /*

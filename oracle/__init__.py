@@ -17,6 +17,9 @@ Functions and the passage of GHOST (arxiv 1507.08101) each one follows:
   application of Sec. "Introduction"); :func:`mixed_precision_cg` -- iterative
   refinement around a float32 inner solve.
 * :func:`round_values` -- float32 and bfloat16 storage rounding.
+* :func:`tsmttsm`, :func:`tsmm` -- the tall and skinny block-vector kernels of
+  the dense-matrix section (X <- alpha V^T W + beta X, W <- alpha V X + beta W),
+  by their definition with numpy's matrix product.
 * :func:`kpm_moments` -- Chebyshev moments mu_k = <x, T_k(A~) x> of the kernel
   polynomial method that Sec. "Kernel fusion" names as the solver the fused
   product serves (A. Weisse, G. Wellein, A. Alvermann and H. Fehske, "The
@@ -370,4 +373,24 @@ def kpm_moments(A, X, nmom: int, a: float, b: float):
         mu[k] = (w0 * nxt).sum(0)
         prev, cur = cur, nxt
     return mu
+
+
+# --------------------------------------------------------------------------- tall and skinny kernels
+
+def tsmttsm(V, W, X0=None, alpha=1.0, beta=0.0):
+    """alpha V^T W + beta X0 in float64."""
+    V = np.asarray(V, np.float64)
+    W = np.asarray(W, np.float64)
+    out = alpha * (V.T @ W)
+    if beta != 0.0:
+        out = out + beta * np.asarray(X0, np.float64)
+    return out
+
+
+def tsmm(V, X, W0=None, alpha=1.0, beta=0.0):
+    """alpha V X + beta W0 in float64."""
+    out = alpha * (np.asarray(V, np.float64) @ np.asarray(X, np.float64))
+    if beta != 0.0:
+        out = out + beta * np.asarray(W0, np.float64)
+    return out
 

@@ -111,6 +111,8 @@ _SIGS = {
                             ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.c_double, ct.c_double, P, P]),
     "sp_kpm_moments": (I, [P, P, I32, ct.c_double, ct.c_double, P, P]),
     "sp_mat_permute": (I, [P, P, P, I, P]),
+    "sp_tsmttsm": (I, [P, P, P, ct.c_double, ct.c_double, I, P]),
+    "sp_tsmm": (I, [P, P, P, ct.c_double, ct.c_double, P]),
     "sp_host_plan_create": (I, [PP, P, I32, I]),
     "sp_spmv_host": (I, [P, P, P, P, P, P, P, ct.POINTER(sp_spmv_opts)]),
     "sp_host_plan_sync": (I, [P]),
@@ -424,6 +426,34 @@ def mat_permute(A: SellMatrix, out, inp, to_sell: bool, stream=None):
         L.sp_dense_destroy(ho, None)
         L.sp_dense_destroy(hi, None)
     return out
+
+
+def tsmttsm(X, V, W, alpha=1.0, beta=0.0, kahan=False, stream=None):
+    """X <- alpha V^T W + beta X (sp_tsmttsm); CUDA tensors, row-major."""
+    L = lib()
+    hx, hv, hw = sp_dense_view(X), sp_dense_view(V), sp_dense_view(W)
+    try:
+        check(L.sp_tsmttsm(hx, hv, hw, float(alpha), float(beta), 1 if kahan else 0, _stream(stream)), "sp_tsmttsm")
+    finally:
+        for h in (hx, hv, hw):
+            L.sp_dense_destroy(h, None)
+    return X
+
+
+def tsmm(W, V, X, alpha=1.0, beta=0.0, stream=None):
+    """W <- alpha V X + beta W (sp_tsmm; W may be V); CUDA tensors, row-major."""
+    L = lib()
+    hw = sp_dense_view(W)
+    hv = hw if V.data_ptr() == W.data_ptr() else sp_dense_view(V)
+    hx = sp_dense_view(X)
+    try:
+        check(L.sp_tsmm(hw, hv, hx, float(alpha), float(beta), _stream(stream)), "sp_tsmm")
+    finally:
+        L.sp_dense_destroy(hw, None)
+        if hv is not hw:
+            L.sp_dense_destroy(hv, None)
+        L.sp_dense_destroy(hx, None)
+    return W
 
 
 def kpm_moments(A: SellMatrix, x, nmom: int, a: float, b: float, stream=None) -> np.ndarray:

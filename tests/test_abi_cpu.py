@@ -66,6 +66,8 @@ def test_host_argument_checks(L):
     assert L.sp_mat_create_csr(ct.byref(h), 1, 2, rp, None, None, 32, 1, 0, s.SP_MAT_PERMUTED_SPACE,
                                None) == s.SP_ERR_DIM  # square only
     assert L.sp_mat_permute(None, None, None, 1, None) == s.SP_ERR_ARG
+    assert L.sp_tsmttsm(None, None, None, 1.0, 0.0, 0, None) == s.SP_ERR_ARG
+    assert L.sp_tsmm(None, None, None, 1.0, 0.0, None) == s.SP_ERR_ARG
     both = s.SP_MAT_ORDER_FRONT | s.SP_MAT_ORDER_RANGES  # at most one work order
     assert L.sp_mat_create_csr(ct.byref(h), 1, 1, rp, None, None, 32, 1, 0, both, None) == s.SP_ERR_ARG
     # dense views: ld too small, bf16 vectors, null pointer
