@@ -564,11 +564,11 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
         std::copy(o.gamma, o.gamma + w, gam.begin());
 
     bool host_dot = (f & SP_SPMV_DOT_HOST) && (f & SP_SPMV_DOT_ANY);
-    DevBufPtr ddot;
+    Tmp ddot(s);  // stream-ordered
     double *dot = o.dot;
     if (host_dot) {
-        SP_TRY(dev_alloc(ddot, 3 * (size_t)w * sizeof(double), s));
-        dot = (double *)ddot->ptr;
+        SP_TRY(ddot.alloc(3 * (size_t)w * sizeof(double)));
+        dot = ddot.as<double>();
     }
     SpmvLaunch L;
     L.P = &P;

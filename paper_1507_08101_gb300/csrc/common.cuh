@@ -40,6 +40,28 @@ struct DevBuf {
 using DevBufPtr = std::shared_ptr<DevBuf>;
 int dev_alloc(DevBufPtr &out, size_t bytes, cudaStream_t s);
 
+// Temporary device buffer (stream-ordered allocation, freed on the stream).
+struct Tmp {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit Tmp(cudaStream_t st) : s(st) {}
+    int alloc(size_t bytes) {
+        if (!bytes) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA;
+        }
+        return SP_OK;
+    }
+    ~Tmp() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    template <class T>
+    T *as() const { return (T *)p; }
+};
+
 // SELL-C-sigma pattern: everything except the values.
 struct Pattern {
     int64_t nrows = 0, ncols = 0, nnz = 0;

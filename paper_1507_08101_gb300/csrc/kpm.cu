@@ -42,8 +42,6 @@ __global__ void k_kpm_assemble(const double *__restrict__ d, int w, int nmom, do
 
 }  // namespace sp
 
-using sp::DevBufPtr;
-
 int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, double b, double *mu, void *stream) {
     if (!A || !x || !mu || nmom < 1) return SP_ERR_ARG;
     if (!(a != 0.0) || !std::isfinite(a) || !std::isfinite(b)) return SP_ERR_ARG;
@@ -56,13 +54,16 @@ int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, d
     // steps: step 0 gives mu_0..mu_2, step n >= 1 gives mu_{2n+1}, mu_{2n+2}
     const int K = nmom - 1;
     const int nsteps = 1 + std::max(0, (K - 2 + 1) / 2);
-    sp_dense *u = nullptr, *v = nullptr;
-    int rc = sp_dense_create(&u, P.nrows, w, x->dtype, SP_ROW_MAJOR, stream);
-    if (rc == SP_OK) rc = sp_dense_create(&v, P.nrows, w, x->dtype, SP_ROW_MAJOR, stream);
-    DevBufPtr dots, dmu;
-    if (rc == SP_OK) rc = sp::dev_alloc(dots, (size_t)nsteps * 3 * w * sizeof(double), s);
-    if (rc == SP_OK) rc = sp::dev_alloc(dmu, (size_t)nmom * w * sizeof(double), s);
+    // working memory is stream-ordered, so a call does not synchronise the device
     const size_t xs = x->dtype == SP_F64 ? 8 : 4;
+    sp::Tmp ub(s), vb(s), dots(s), dmu(s);
+    int rc = ub.alloc((size_t)P.nrows * w * xs);
+    if (rc == SP_OK) rc = vb.alloc((size_t)P.nrows * w * xs);
+    if (rc == SP_OK) rc = dots.alloc((size_t)nsteps * 3 * w * sizeof(double));
+    if (rc == SP_OK) rc = dmu.alloc((size_t)nmom * w * sizeof(double));
+    sp_dense *u = nullptr, *v = nullptr;
+    if (rc == SP_OK) rc = sp_dense_view(&u, ub.p, P.nrows, w, w, x->dtype, SP_ROW_MAJOR);
+    if (rc == SP_OK) rc = sp_dense_view(&v, vb.p, P.nrows, w, w, x->dtype, SP_ROW_MAJOR);
     if (rc == SP_OK) {
         cudaError_t e = cudaMemcpy2DAsync(u->ptr, (size_t)w * xs, x->ptr, (size_t)x->ld * xs, (size_t)w * xs,
                                           (size_t)P.nrows, cudaMemcpyDeviceToDevice, s);
@@ -71,7 +72,7 @@ int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, d
             rc = SP_ERR_CUDA;
         }
     }
-    double *d = rc == SP_OK ? (double *)dots->ptr : nullptr;
+    double *d = rc == SP_OK ? dots.as<double>() : nullptr;
     const double gamma = b;
     for (int n = 0; n < nsteps && rc == SP_OK; ++n) {
         sp_spmv_opts o = SP_SPMV_OPTS_INIT;
@@ -93,10 +94,10 @@ int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, d
     }
     if (rc == SP_OK) {
         const int threads = 256, blocks = std::max(1, std::min(1024, (nmom * w + threads - 1) / threads));
-        sp::k_kpm_assemble<<<blocks, threads, 0, s>>>(d, w, nmom, (double *)dmu->ptr);
+        sp::k_kpm_assemble<<<blocks, threads, 0, s>>>(d, w, nmom, dmu.as<double>());
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(mu, dmu->ptr, (size_t)nmom * w * sizeof(double), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(mu, dmu.p, (size_t)nmom * w * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             sp_internal_note_cuda_error(e, "kpm moments", __FILE__, __LINE__);
@@ -105,7 +106,7 @@ int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, d
     } else {
         cudaStreamSynchronize(s);
     }
-    if (u) sp_dense_destroy(u, stream);
+    if (u) sp_dense_destroy(u, stream);  // views: the memory goes back with ub, vb
     if (v) sp_dense_destroy(v, stream);
     return rc;
 }

@@ -5,13 +5,29 @@
 //     tsmm:     W <- alpha V X + beta W      (also in place, W = V, k = m)
 // Row-major blocks on the device, m, k <= 32.  Both stream V and W once.
 //
-// tsmttsm: each block takes a contiguous range of rows in tiles of kTileRows,
-// staged in shared memory; each thread owns up to four of the m*k outputs and
-// adds that tile's products into them.  The per-block sums go to a partial
-// array and a second kernel adds them in block order, so the result does not
-// depend on timing.  tsmm: each block stages a tile of rows of V, computes the
-// tile's rows of the result from the small matrix in shared memory, and only
-// then writes, so the in-place form reads every row before it overwrites it.
+// The paper notes that these products should be memory bound for large n.
+// On this GPU that holds in float32; in float64 the FP64 pipe (2 fused
+// multiply-adds per SM and cycle) binds once m * k reaches a few dozen, so the
+// kernels aim at keeping that pipe busy rather than at fewer bytes.
+//
+// Both kernels stream tiles of rows into shared memory with cp.async through a
+// ring of kTsmStages buffers: while a block works on tile i the copies of
+// tiles i + 1 .. i + kTsmStages - 1 are in flight.  Each block takes a
+// contiguous run of tiles.
+//
+// tsmttsm: each thread owns an RA x RB block of the outputs; LA x LB threads
+// cover the (padded) m x k result and the 256 / (LA LB) groups of such threads
+// take different rows of the tile.  Per row a thread reads RA values of V and
+// RB values of W (vector loads from shared memory) and does RA RB multiply-adds
+// (or Kahan steps).  The groups are summed in a fixed order inside the block,
+// the blocks in a fixed order by a second kernel, so results do not depend on
+// timing; the Kahan variant carries (sum, compensation) pairs through both
+// reductions.
+//
+// tsmm: each thread keeps an MP x RB slice of X in registers and produces RB
+// outputs of one row at a time from the row of V in shared memory; a row of W
+// is written only after its tile of V is in shared memory, so the in-place
+// form reads every row before it overwrites it.
 #include <algorithm>
 
 #include "common.cuh"
@@ -19,140 +35,410 @@
 namespace sp {
 
 constexpr int kTsmThreads = 256;
-constexpr int kTileRows = 32;
 constexpr int kTsmMax = 32;
-constexpr int kPerThread = kTsmMax * kTsmMax / kTsmThreads;  // outputs per thread (4)
+constexpr int kTsmStages = 2;           // tiles per block in shared memory (ring)
+constexpr int kTsmTileBytes = 24576;    // bytes of V (and W) per staged tile
+constexpr int kTsmMaxBlocksPerSm = 4;
+constexpr size_t kTsmSmemMax = 48 * 1024;  // dynamic shared memory without an opt-in attribute
 
-template <class T, bool KAHAN>
-__global__ void __launch_bounds__(kTsmThreads) k_tsmttsm_part(const T *__restrict__ V, int64_t ldv,
+// ------------------------------------------------------------------ cp.async staging
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy rows [row0, row0 + rows) x columns [0, cols) of a row-major block with
+// leading dimension ld into shared memory with row stride dstride.  vec: every
+// row is a whole number of 16-byte pieces, 16-byte aligned on both sides.
+template <class T>
+__device__ __forceinline__ void stage_rows(T *dst, int dstride, const T *__restrict__ src, int64_t ld,
+                                           int64_t row0, int rows, int cols, bool vec) {
+    const int e0 = threadIdx.x;
+    if (vec) {
+        constexpr int E = 16 / sizeof(T);
+        const int cpr = cols / E;  // 16-byte pieces per row
+        int r = e0 / cpr, c = e0 - r * cpr;
+        const int dr = kTsmThreads / cpr, dc = kTsmThreads - dr * cpr;
+        while (r < rows) {
+            cp_async<16>(dst + r * dstride + c * E, src + (row0 + r) * ld + c * E);
+            r += dr;
+            c += dc;
+            if (c >= cpr) {
+                c -= cpr;
+                ++r;
+            }
+        }
+    } else {
+        int r = e0 / cols, c = e0 - r * cols;
+        const int dr = kTsmThreads / cols, dc = kTsmThreads - dr * cols;
+        while (r < rows) {
+            cp_async<(int)sizeof(T)>(dst + r * dstride + c, src + (row0 + r) * ld + c);
+            r += dr;
+            c += dc;
+            if (c >= cols) {
+                c -= cols;
+                ++r;
+            }
+        }
+    }
+}
+
+// N consecutive elements from 16-byte-aligned (N * sizeof(T) >= 16) or
+// N * sizeof(T)-aligned shared memory.
+template <class T, int N>
+__device__ __forceinline__ void ld_vec(const T *p, T *out) {
+    constexpr int B = N * (int)sizeof(T);
+    if constexpr (B >= 16) {
+        constexpr int E = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < N / E; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + q * E);
+            const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int i = 0; i < E; ++i) out[q * E + i] = pv[i];
+        }
+    } else if constexpr (B == 8) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = pv[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = p[i];
+    }
+}
+
+// (sum, compensation) pair: the represented value is s + c.  merge adds
+// another pair with the exact error of s1 + s2 (Knuth's TwoSum) kept in c.
+struct Comp {
+    double s, c;
+};
+__device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
+    const double t = a.s + b.s;
+    const double bv = t - a.s;
+    const double e = (a.s - (t - bv)) + (b.s - bv);
+    return Comp{t, (a.c + b.c) + e};
+}
+
+// Rows per staged tile for `row_bytes` bytes of shared memory per row.
+inline int tile_rows(int row_bytes) {
+    int tr = kTsmTileBytes / row_bytes;
+    tr = std::max(32, std::min(1024, tr / 32 * 32));
+    return tr;
+}
+
+// ------------------------------------------------------------------ tsmttsm
+// part[(a * k + b) * nb + block] = (s, c) of the block's sum for output (a, b)
+template <class T, bool KAHAN, int RA, int RB, int LA, int LB>
+__global__ void __launch_bounds__(kTsmThreads) k_tsmttsm_tile(const T *__restrict__ V, int64_t ldv,
                                                               const T *__restrict__ W, int64_t ldw, int64_t n, int m,
-                                                              int k, int64_t rows_per_block, double *__restrict__ part) {
-    __shared__ T sv[kTileRows][kTsmMax], sw[kTileRows][kTsmMax];
-    const int t = threadIdx.x;
-    T acc[kPerThread], comp[kPerThread];
+                                                              int k, int tr, int64_t tiles_per_block, int vec,
+                                                              Comp *__restrict__ part) {
+    constexpr int L = LA * LB, G = kTsmThreads / L, MPs = LA * RA, KPs = LB * RB, RR = RA * RB;
+    extern __shared__ __align__(16) unsigned char tsm_smem[];
+    T *const st = reinterpret_cast<T *>(tsm_smem);
+    const int t = threadIdx.x, l = t % L, g = t / L, ia = l / LB, ib = l % LB;
+    const int stage_elems = tr * (MPs + KPs);
+    // padding columns (never written by the copies) hold zeros
+    for (int e = t; e < kTsmStages * stage_elems; e += kTsmThreads) {
+        const int o = e % stage_elems;
+        const bool pad = o < tr * MPs ? (o % MPs) >= m : ((o - tr * MPs) % KPs) >= k;
+        if (pad) st[e] = T(0);
+    }
+    T acc[RR], cmp[RR];
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) acc[j] = comp[j] = T(0);
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r1 = n < r0 + rows_per_block ? n : r0 + rows_per_block;
-    const int mk = m * k;
-    for (int64_t base = r0; base < r1; base += kTileRows) {
-        const int rows = (int)(r1 - base < kTileRows ? r1 - base : kTileRows);
-        for (int e = t; e < kTileRows * m; e += kTsmThreads) {
-            const int r = e / m, c = e - r * m;
-            sv[r][c] = r < rows ? V[(base + r) * ldv + c] : T(0);
-        }
-        for (int e = t; e < kTileRows * k; e += kTsmThreads) {
-            const int r = e / k, c = e - r * k;
-            sw[r][c] = r < rows ? W[(base + r) * ldw + c] : T(0);
-        }
+    for (int x = 0; x < RR; ++x) acc[x] = cmp[x] = T(0);
+    const int64_t ntiles = (n + tr - 1) / tr;
+    const int64_t tile0 = (int64_t)blockIdx.x * tiles_per_block;
+    const int64_t tile1 = ntiles < tile0 + tiles_per_block ? ntiles : tile0 + tiles_per_block;
+    auto stage = [&](int64_t tile, int s) {
+        T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
+        const int64_t r0 = tile * tr;
+        const int rows = (int)(n - r0 < tr ? n - r0 : tr);
+        stage_rows(sv, MPs, V, ldv, r0, rows, m, vec & 1);
+        stage_rows(sw, KPs, W, ldw, r0, rows, k, (vec & 2) != 0);
+    };
+    // one commit group per tile (empty past the end), so that waiting for all
+    // but the newest kTsmStages - 1 groups leaves this tile complete
+#pragma unroll
+    for (int i = 0; i < kTsmStages - 1; ++i) {
+        if (tile0 + i < tile1) stage(tile0 + i, i);
+        cp_async_commit();
+    }
+    for (int64_t tile = tile0; tile < tile1; ++tile) {
+        const int it = (int)(tile - tile0), s = it % kTsmStages;
+        if (tile + kTsmStages - 1 < tile1) stage(tile + kTsmStages - 1, (it + kTsmStages - 1) % kTsmStages);
+        cp_async_commit();
+        cp_async_wait<kTsmStages - 1>();
         __syncthreads();
+        const T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
+        const int rows = (int)(n - tile * tr < tr ? n - tile * tr : tr);
+        for (int r = g; r < rows; r += G) {
+            T va[RA], wb[RB];
+            ld_vec<T, RA>(sv + r * MPs + ia * RA, va);
+            ld_vec<T, RB>(sw + r * KPs + ib * RB, wb);
 #pragma unroll
-        for (int j = 0; j < kPerThread; ++j) {
-            const int e = t + j * kTsmThreads;
-            if (e < mk) {
-                const int a = e / k, b = e - a * k;
-                for (int r = 0; r < rows; ++r) {
-                    const T p = sv[r][a] * sw[r][b];
+            for (int i = 0; i < RA; ++i)
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    const int x = i * RB + j;
                     if constexpr (KAHAN) {
-                        // Kahan's compensated summation: comp carries the
+                        // Kahan's compensated summation: cmp carries the
                         // low-order part lost by the last addition
-                        const T yv = p - comp[j];
-                        const T tv = acc[j] + yv;
-                        comp[j] = (tv - acc[j]) - yv;
-                        acc[j] = tv;
+                        const T yv = va[i] * wb[j] - cmp[x];
+                        const T tv = acc[x] + yv;
+                        cmp[x] = (tv - acc[x]) - yv;
+                        acc[x] = tv;
                     } else {
-                        acc[j] = fma(sv[r][a], sw[r][b], acc[j]);
+                        acc[x] = fma(va[i], wb[j], acc[x]);
                     }
                 }
+        }
+        __syncthreads();
+    }
+    // row groups inside a warp (lanes l, l + L, ...): fixed xor tree
+    Comp cs[RR];
+#pragma unroll
+    for (int x = 0; x < RR; ++x) cs[x] = Comp{(double)acc[x], KAHAN ? -(double)cmp[x] : 0.0};
+#pragma unroll
+    for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+        for (int x = 0; x < RR; ++x) {
+            const Comp o{__shfl_xor_sync(0xffffffffu, cs[x].s, off), __shfl_xor_sync(0xffffffffu, cs[x].c, off)};
+            if constexpr (KAHAN)
+                cs[x] = comp_merge(cs[x], o);
+            else
+                cs[x].s += o.s;
+        }
+    // the block's warps in order, into shared memory (reusing the tiles)
+    Comp *red = reinterpret_cast<Comp *>(tsm_smem);
+    const int warp = t >> 5, lane = t & 31;
+    for (int w = 0; w < kTsmThreads / 32; ++w) {
+        if (warp == w && lane < L) {
+#pragma unroll
+            for (int x = 0; x < RR; ++x) {
+                Comp &d = red[lane * RR + x];
+                if (w == 0)
+                    d = cs[x];
+                else if (KAHAN)
+                    d = comp_merge(d, cs[x]);
+                else
+                    d.s += cs[x].s;
             }
         }
         __syncthreads();
     }
-#pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        const int e = t + j * kTsmThreads;
-        if (e < mk) part[(int64_t)blockIdx.x * mk + e] = (double)acc[j] - (KAHAN ? (double)comp[j] : 0.0);
+    const int nb = gridDim.x;
+    for (int o = t; o < L * RR; o += kTsmThreads) {
+        const int ll = o / RR, x = o - ll * RR;
+        const int a = (ll / LB) * RA + x / RB, b = (ll % LB) * RB + x % RB;
+        if (a < m && b < k) part[(int64_t)(a * k + b) * nb + blockIdx.x] = red[o];
     }
 }
 
-// X[a, b] = alpha * sum over blocks (in block order) + beta X[a, b]
+// X[a, b] = alpha * (sum over blocks, in order) + beta X[a, b]: one warp per output
 template <class T, bool KAHAN>
-__global__ void k_tsmttsm_final(const double *__restrict__ part, int nblocks, int m, int k, double alpha,
-                                double beta, T *__restrict__ X, int64_t ldx) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * k) return;
-    double s = 0.0, c = 0.0;
-    for (int bl = 0; bl < nblocks; ++bl) {
-        const double p = part[(int64_t)bl * m * k + e];
-        if constexpr (KAHAN) {
-            const double yv = p - c;
-            const double tv = s + yv;
-            c = (tv - s) - yv;
-            s = tv;
-        } else {
-            s += p;
-        }
+__global__ void k_tsmttsm_final(const Comp *__restrict__ part, int nb, int m, int k, double alpha, double beta,
+                                T *__restrict__ X, int64_t ldx) {
+    const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (e >= m * k) return;  // whole warps leave together
+    const Comp *p = part + (int64_t)e * nb;
+    Comp acc{0.0, 0.0};
+    for (int bl = lane; bl < nb; bl += 32) {
+        if constexpr (KAHAN)
+            acc = comp_merge(acc, p[bl]);
+        else
+            acc.s += p[bl].s;
     }
-    const int a = e / k, b = e - a * k;
-    T *xp = X + (int64_t)a * ldx + b;
-    const double old = beta != 0.0 ? (double)*xp : 0.0;
-    *xp = (T)(alpha * s + beta * old);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Comp o{__shfl_xor_sync(0xffffffffu, acc.s, off), __shfl_xor_sync(0xffffffffu, acc.c, off)};
+        if constexpr (KAHAN)
+            acc = comp_merge(acc, o);
+        else
+            acc.s += o.s;
+    }
+    if (lane == 0) {
+        const int a = e / k, b = e - a * k;
+        T *xp = X + (int64_t)a * ldx + b;
+        const double old = beta != 0.0 ? (double)*xp : 0.0;
+        *xp = (T)(alpha * (acc.s + acc.c) + beta * old);
+    }
+}
+
+// ------------------------------------------------------------------ tsmm
+// Lanes per row LB = 2^lbs cover the k outputs of a row in slices of RB; the
+// 256 / LB rows a block works on at once are the row groups.
+template <class T, int MP, int RB>
+__global__ void __launch_bounds__(kTsmThreads) k_tsmm_tile(const T *__restrict__ V, int64_t ldv,
+                                                           const T *__restrict__ X, int64_t ldx, T *W, int64_t ldw,
+                                                           int64_t n, int m, int k, int lbs, int tr,
+                                                           int64_t tiles_per_block, int vec, T alpha, T beta) {
+    constexpr int VW = 16 / (int)sizeof(T);  // elements per 16-byte shared-memory load
+    constexpr int MPs = MP + VW;             // padded row stride of the V tile (spreads rows over banks)
+    extern __shared__ __align__(16) unsigned char tsm_smem[];
+    T *const st = reinterpret_cast<T *>(tsm_smem);
+    const int t = threadIdx.x, q = t & ((1 << lbs) - 1), g = t >> lbs, G = kTsmThreads >> lbs;
+    const int b0 = q * RB;
+    T xr[MP][RB];
+#pragma unroll
+    for (int a = 0; a < MP; ++a)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) xr[a][j] = (a < m && b0 + j < k) ? X[(int64_t)a * ldx + b0 + j] : T(0);
+    const int stage_elems = tr * MPs;
+    for (int e = t; e < kTsmStages * stage_elems; e += kTsmThreads)
+        if ((e % MPs) >= m) st[e] = T(0);  // padding columns: zeros (0 x 0 in the products)
+    const int64_t ntiles = (n + tr - 1) / tr;
+    const int64_t tile0 = (int64_t)blockIdx.x * tiles_per_block;
+    const int64_t tile1 = ntiles < tile0 + tiles_per_block ? ntiles : tile0 + tiles_per_block;
+    auto stage = [&](int64_t tile, int s) {
+        const int64_t r0 = tile * tr;
+        const int rows = (int)(n - r0 < tr ? n - r0 : tr);
+        stage_rows(st + s * stage_elems, MPs, V, ldv, r0, rows, m, vec != 0);
+    };
+#pragma unroll
+    for (int i = 0; i < kTsmStages - 1; ++i) {
+        if (tile0 + i < tile1) stage(tile0 + i, i);
+        cp_async_commit();
+    }
+    for (int64_t tile = tile0; tile < tile1; ++tile) {
+        const int it = (int)(tile - tile0), s = it % kTsmStages;
+        if (tile + kTsmStages - 1 < tile1) stage(tile + kTsmStages - 1, (it + kTsmStages - 1) % kTsmStages);
+        cp_async_commit();
+        cp_async_wait<kTsmStages - 1>();
+        __syncthreads();  // the tile of V is in shared memory before W (which may be V) is written
+        const T *sv = st + s * stage_elems;
+        const int64_t r0 = tile * tr;
+        const int rows = (int)(n - r0 < tr ? n - r0 : tr);
+        for (int r = g; r < rows; r += G) {
+            T out[RB];
+#pragma unroll
+            for (int j = 0; j < RB; ++j) out[j] = T(0);
+#pragma unroll
+            for (int a0 = 0; a0 < MP; a0 += VW) {
+                T v[VW];
+                ld_vec<T, VW>(sv + r * MPs + a0, v);
+#pragma unroll
+                for (int i = 0; i < VW; ++i)
+#pragma unroll
+                    for (int j = 0; j < RB; ++j) out[j] = fma(v[i], xr[a0 + i][j], out[j]);
+            }
+            T *wp = W + (r0 + r) * ldw + b0;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+                if (b0 + j < k) {
+                    const T old = beta != T(0) ? wp[j] : T(0);
+                    wp[j] = fma(alpha, out[j], beta * old);
+                }
+        }
+        __syncthreads();  // before the next copies overwrite this stage
+    }
+}
+
+static int sms_count() {
+    int sms = 1;
+    device_sm_count(&sms);
+    return sms;
+}
+
+// blocks for a grid of contiguous tile runs: SMs x resident blocks (at most
+// kTsmMaxBlocksPerSm), no more than there are tiles
+template <class K>
+static int tsm_grid(K kernel, size_t smem, int64_t ntiles, int64_t *tiles_per_block) {
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kTsmThreads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int64_t want = (int64_t)sms_count() * std::min(occ, kTsmMaxBlocksPerSm);
+    const int64_t nb0 = std::max<int64_t>(1, std::min<int64_t>(want, ntiles));
+    *tiles_per_block = (ntiles + nb0 - 1) / nb0;
+    return (int)std::max<int64_t>(1, (ntiles + *tiles_per_block - 1) / *tiles_per_block);
+}
+
+static bool vec16_ok(const void *p, int64_t ld, int cols, size_t es) {
+    return ((uintptr_t)p % 16) == 0 && (ld * es) % 16 == 0 && (cols * es) % 16 == 0;
+}
+
+template <class T, bool KAHAN, int RA, int RB, int LA, int LB>
+static int run_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *Wd, double alpha, double beta,
+                       cudaStream_t s) {
+    constexpr int L = LA * LB, RR = RA * RB, MPs = LA * RA, KPs = LB * RB;
+    const int64_t n = V->nrows;
+    const int m = V->ncols, k = Wd->ncols;
+    const int tr = tile_rows((MPs + KPs) * (int)sizeof(T));
+    const size_t smem = std::max<size_t>((size_t)kTsmStages * tr * (MPs + KPs) * sizeof(T), (size_t)L * RR * sizeof(Comp));
+    const int64_t ntiles = std::max<int64_t>(1, (n + tr - 1) / tr);
+    if (smem > kTsmSmemMax) return SP_ERR_UNSUPPORTED;  // not reached: tiles hold at most kTsmTileBytes
+    auto kern = k_tsmttsm_tile<T, KAHAN, RA, RB, LA, LB>;
+    int64_t tpb = 1;
+    const int nb = tsm_grid(kern, smem, ntiles, &tpb);
+    Tmp part(s);  // stream-ordered: no device-wide synchronisation per call
+    SP_TRY(part.alloc((size_t)nb * m * k * sizeof(Comp)));
+    const int vec = (vec16_ok(V->ptr, V->ld, m, sizeof(T)) ? 1 : 0) | (vec16_ok(Wd->ptr, Wd->ld, k, sizeof(T)) ? 2 : 0);
+    kern<<<nb, kTsmThreads, smem, s>>>((const T *)V->ptr, V->ld, (const T *)Wd->ptr, Wd->ld, n, m, k, tr, tpb, vec,
+                                       part.as<Comp>());
+    const int fin_blocks = (m * k * 32 + 255) / 256;
+    k_tsmttsm_final<T, KAHAN><<<fin_blocks, 256, 0, s>>>(part.as<const Comp>(), nb, m, k, alpha, beta, (T *)X->ptr,
+                                                         X->ld);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+template <class T, bool KAHAN>
+static int dispatch_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, double beta,
+                            cudaStream_t s) {
+    const int p = std::max(V->ncols, W->ncols);
+    if (p <= 2) return run_tsmttsm<T, KAHAN, 2, 2, 1, 1>(X, V, W, alpha, beta, s);
+    if (p <= 4) return run_tsmttsm<T, KAHAN, 4, 4, 1, 1>(X, V, W, alpha, beta, s);
+    if (p <= 8) return run_tsmttsm<T, KAHAN, 4, 4, 2, 2>(X, V, W, alpha, beta, s);
+    if (p <= 16) return run_tsmttsm<T, KAHAN, 4, 4, 4, 4>(X, V, W, alpha, beta, s);
+    return run_tsmttsm<T, KAHAN, 4, 8, 8, 4>(X, V, W, alpha, beta, s);
+}
+
+template <class T, int MP>
+static int run_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, double beta, cudaStream_t s) {
+    // slices of X in registers: MP x RB values per thread
+    constexpr int RB = (sizeof(T) == 8 && MP == 32) ? 2 : 4;
+    constexpr int MPs = MP + 16 / (int)sizeof(T);
+    const int64_t n = V->nrows;
+    const int m = V->ncols, k = W->ncols;
+    int lbs = 0;
+    while ((1 << lbs) * RB < k) ++lbs;
+    const int tr = tile_rows(MPs * (int)sizeof(T));
+    const size_t smem = (size_t)kTsmStages * tr * MPs * sizeof(T);
+    const int64_t ntiles = std::max<int64_t>(1, (n + tr - 1) / tr);
+    if (smem > kTsmSmemMax) return SP_ERR_UNSUPPORTED;
+    auto kern = k_tsmm_tile<T, MP, RB>;
+    int64_t tpb = 1;
+    const int nb = tsm_grid(kern, smem, ntiles, &tpb);
+    const int vec = vec16_ok(V->ptr, V->ld, m, sizeof(T)) ? 1 : 0;
+    kern<<<nb, kTsmThreads, smem, s>>>((const T *)V->ptr, V->ld, (const T *)X->ptr, X->ld, (T *)W->ptr, W->ld, n, m,
+                                       k, lbs, tr, tpb, vec, (T)alpha, (T)beta);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
 }
 
 template <class T>
-__global__ void __launch_bounds__(kTsmThreads) k_tsmm(const T *__restrict__ V, int64_t ldv, const T *__restrict__ X,
-                                                      int64_t ldx, T *W, int64_t ldw, int64_t n, int m, int k,
-                                                      T alpha, T beta) {
-    __shared__ T sx[kTsmMax][kTsmMax];
-    __shared__ T sv[kTileRows][kTsmMax];
-    const int t = threadIdx.x;
-    for (int e = t; e < m * k; e += kTsmThreads) {
-        const int a = e / k, b = e - a * k;
-        sx[a][b] = X[(int64_t)a * ldx + b];
-    }
-    for (int64_t base = (int64_t)blockIdx.x * kTileRows; base < n; base += (int64_t)gridDim.x * kTileRows) {
-        const int rows = (int)(n - base < kTileRows ? n - base : kTileRows);
-        for (int e = t; e < kTileRows * m; e += kTsmThreads) {
-            const int r = e / m, c = e - r * m;
-            sv[r][c] = r < rows ? V[(base + r) * ldv + c] : T(0);
-        }
-        __syncthreads();  // the tile of V is read before W (which may be V) is written
-        T out[kPerThread];
-#pragma unroll
-        for (int j = 0; j < kPerThread; ++j) {
-            const int e = t + j * kTsmThreads;
-            out[j] = T(0);
-            if (e < kTileRows * k) {
-                const int r = e / k, b = e - r * k;
-                if (r < rows) {
-                    T s = T(0);
-                    for (int a = 0; a < m; ++a) s = fma(sv[r][a], sx[a][b], s);
-                    const T old = beta != T(0) ? W[(base + r) * ldw + b] : T(0);
-                    out[j] = fma(alpha, s, beta * old);
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kPerThread; ++j) {
-            const int e = t + j * kTsmThreads;
-            if (e < kTileRows * k) {
-                const int r = e / k, b = e - r * k;
-                if (r < rows) W[(base + r) * ldw + b] = out[j];
-            }
-        }
-    }
-}
-
-static int sms_blocks(int per_sm) {
-    int sms = 1;
-    device_sm_count(&sms);
-    return sms * per_sm;
+static int dispatch_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, double beta,
+                         cudaStream_t s) {
+    const int m = V->ncols;
+    if (m <= 4) return run_tsmm<T, 4>(W, V, X, alpha, beta, s);
+    if (m <= 8) return run_tsmm<T, 8>(W, V, X, alpha, beta, s);
+    if (m <= 16) return run_tsmm<T, 16>(W, V, X, alpha, beta, s);
+    return run_tsmm<T, 32>(W, V, X, alpha, beta, s);
 }
 
 }  // namespace sp
-
-using sp::DevBufPtr;
 
 static bool rowmajor_dev(const sp_dense *d) { return d && d->layout == SP_ROW_MAJOR && d->ptr; }
 
@@ -166,35 +452,11 @@ int sp_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, 
     if (m < 1 || k < 1) return SP_ERR_ARG;
     if (m > sp::kTsmMax || k > sp::kTsmMax) return SP_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = V->nrows;
-    int nb = (int)std::max<int64_t>(1, std::min<int64_t>(sp::sms_blocks(4), (n + sp::kTileRows - 1) / sp::kTileRows));
-    const int64_t rpb = std::max<int64_t>(sp::kTileRows,
-                                          ((n + nb - 1) / nb + sp::kTileRows - 1) / sp::kTileRows * sp::kTileRows);
-    nb = (int)std::max<int64_t>(1, (n + rpb - 1) / rpb);
-    DevBufPtr part;
-    SP_TRY(sp::dev_alloc(part, (size_t)nb * m * k * sizeof(double), s));
-    const int fin = (m * k + 255) / 256;
-#define SP_TSM_LAUNCH(T, KH)                                                                                       \
-    sp::k_tsmttsm_part<T, KH><<<nb, sp::kTsmThreads, 0, s>>>((const T *)V->ptr, V->ld, (const T *)W->ptr, W->ld, n, \
-                                                             m, k, rpb, (double *)part->ptr);                         \
-    sp::k_tsmttsm_final<T, KH><<<fin, 256, 0, s>>>((const double *)part->ptr, nb, m, k, alpha, beta, (T *)X->ptr,   \
-                                                   X->ld);
-    if (V->dtype == SP_F64) {
-        if (kahan) {
-            SP_TSM_LAUNCH(double, true)
-        } else {
-            SP_TSM_LAUNCH(double, false)
-        }
-    } else {
-        if (kahan) {
-            SP_TSM_LAUNCH(float, true)
-        } else {
-            SP_TSM_LAUNCH(float, false)
-        }
-    }
-#undef SP_TSM_LAUNCH
-    SP_CUDA(cudaGetLastError());
-    return SP_OK;
+    if (V->dtype == SP_F64)
+        return kahan ? sp::dispatch_tsmttsm<double, true>(X, V, W, alpha, beta, s)
+                     : sp::dispatch_tsmttsm<double, false>(X, V, W, alpha, beta, s);
+    return kahan ? sp::dispatch_tsmttsm<float, true>(X, V, W, alpha, beta, s)
+                 : sp::dispatch_tsmttsm<float, false>(X, V, W, alpha, beta, s);
 }
 
 int sp_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, double beta, void *stream) {
@@ -216,14 +478,6 @@ int sp_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, dou
     };
     if ((!inplace && overl(W, V)) || overl(W, X)) return SP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = V->nrows;
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(sp::sms_blocks(8), (n + sp::kTileRows - 1) / sp::kTileRows));
-    if (V->dtype == SP_F64)
-        sp::k_tsmm<double><<<nb, sp::kTsmThreads, 0, s>>>((const double *)V->ptr, V->ld, (const double *)X->ptr, X->ld,
-                                                          (double *)W->ptr, W->ld, n, m, k, alpha, beta);
-    else
-        sp::k_tsmm<float><<<nb, sp::kTsmThreads, 0, s>>>((const float *)V->ptr, V->ld, (const float *)X->ptr, X->ld,
-                                                         (float *)W->ptr, W->ld, n, m, k, (float)alpha, (float)beta);
-    SP_CUDA(cudaGetLastError());
-    return SP_OK;
+    if (V->dtype == SP_F64) return sp::dispatch_tsmm<double>(W, V, X, alpha, beta, s);
+    return sp::dispatch_tsmm<float>(W, V, X, alpha, beta, s);
 }
