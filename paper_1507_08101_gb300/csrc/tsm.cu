@@ -10,9 +10,9 @@
 // multiply-adds per SM and cycle) binds once m * k reaches a few dozen, so the
 // kernels aim at keeping that pipe busy rather than at fewer bytes.
 //
-// Both kernels stream tiles of rows into shared memory with cp.async through a
-// ring of kTsmStages buffers: while a block works on tile i the copies of
-// tiles i + 1 .. i + kTsmStages - 1 are in flight.  Each block takes a
+// Both kernels stream tiles of rows into shared memory with cp.async: while a
+// block works on tile i the copy of tile i + 1 is in flight (tsmttsm through a
+// ring of kTsmStages buffers, tsmm through two).  Each block takes a
 // contiguous run of tiles.
 //
 // tsmttsm: each thread owns an RA x RB block of the outputs; LA x LB threads
@@ -94,6 +94,14 @@ __device__ __forceinline__ void stage_rows(T *dst, int dstride, const T *__restr
     }
 }
 
+// Copy `pieces` 16-byte pieces from src to dst (rows that are one contiguous
+// run on both sides: ld == cols == the shared-memory row stride).
+template <class T>
+__device__ __forceinline__ void stage_contig(T *dst, const T *__restrict__ src, int pieces) {
+    constexpr int E = 16 / sizeof(T);
+    for (int e = threadIdx.x; e < pieces; e += kTsmThreads) cp_async<16>(dst + e * E, src + e * E);
+}
+
 // N consecutive elements from 16-byte-aligned (N * sizeof(T) >= 16) or
 // N * sizeof(T)-aligned shared memory.
 template <class T, int N>
@@ -139,9 +147,30 @@ inline int tile_rows(int row_bytes) {
 }
 
 // ------------------------------------------------------------------ tsmttsm
+// acc[i RB + j] += va[i] wb[j] (Kahan: cmp carries the low-order part lost by
+// the last addition of each sum)
+template <class T, bool KAHAN, int RA, int RB>
+__device__ __forceinline__ void outer_acc(T (&acc)[RA * RB], T (&cmp)[RA * RB], const T (&va)[RA],
+                                          const T (&wb)[RB]) {
+#pragma unroll
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            const int x = i * RB + j;
+            if constexpr (KAHAN) {
+                const T yv = va[i] * wb[j] - cmp[x];
+                const T tv = acc[x] + yv;
+                cmp[x] = (tv - acc[x]) - yv;
+                acc[x] = tv;
+            } else {
+                acc[x] = fma(va[i], wb[j], acc[x]);
+            }
+        }
+}
+
 // part[(a * k + b) * nb + block] = (s, c) of the block's sum for output (a, b)
 template <class T, bool KAHAN, int RA, int RB, int LA, int LB>
-__global__ void __launch_bounds__(kTsmThreads) k_tsmttsm_tile(const T *__restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kTsmThreads, RA * RB > 16 ? 1 : (KAHAN ? 2 : 4)) k_tsmttsm_tile(const T *__restrict__ V, int64_t ldv,
                                                               const T *__restrict__ W, int64_t ldw, int64_t n, int m,
                                                               int k, int tr, int64_t tiles_per_block, int vec,
                                                               Comp *__restrict__ part) {
@@ -162,12 +191,20 @@ __global__ void __launch_bounds__(kTsmThreads) k_tsmttsm_tile(const T *__restric
     const int64_t ntiles = (n + tr - 1) / tr;
     const int64_t tile0 = (int64_t)blockIdx.x * tiles_per_block;
     const int64_t tile1 = ntiles < tile0 + tiles_per_block ? ntiles : tile0 + tiles_per_block;
+    // rows of V (W) that are contiguous in memory and fill the tile's rows exactly
+    const bool dense_v = (vec & 1) && ldv == m && MPs == m, dense_w = (vec & 2) && ldw == k && KPs == k;
     auto stage = [&](int64_t tile, int s) {
         T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
         const int64_t r0 = tile * tr;
         const int rows = (int)(n - r0 < tr ? n - r0 : tr);
-        stage_rows(sv, MPs, V, ldv, r0, rows, m, vec & 1);
-        stage_rows(sw, KPs, W, ldw, r0, rows, k, (vec & 2) != 0);
+        if (dense_v)
+            stage_contig(sv, V + r0 * ldv, rows * (MPs * (int)sizeof(T) / 16));
+        else
+            stage_rows(sv, MPs, V, ldv, r0, rows, m, vec & 1);
+        if (dense_w)
+            stage_contig(sw, W + r0 * ldw, rows * (KPs * (int)sizeof(T) / 16));
+        else
+            stage_rows(sw, KPs, W, ldw, r0, rows, k, (vec & 2) != 0);
     };
     // one commit group per tile (empty past the end), so that waiting for all
     // but the newest kTsmStages - 1 groups leaves this tile complete
@@ -184,60 +221,61 @@ __global__ void __launch_bounds__(kTsmThreads) k_tsmttsm_tile(const T *__restric
         __syncthreads();
         const T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
         const int rows = (int)(n - tile * tr < tr ? n - tile * tr : tr);
-        for (int r = g; r < rows; r += G) {
+        // rows g, g + G, ...: two per step
+        const T *pv = sv + g * MPs + ia * RA, *pw = sw + g * KPs + ib * RB;
+        int r = g;
+        for (; r + G < rows; r += 2 * G, pv += 2 * G * MPs, pw += 2 * G * KPs) {
+            T va0[RA], wb0[RB], va1[RA], wb1[RB];
+            ld_vec<T, RA>(pv, va0);
+            ld_vec<T, RB>(pw, wb0);
+            ld_vec<T, RA>(pv + G * MPs, va1);
+            ld_vec<T, RB>(pw + G * KPs, wb1);
+            outer_acc<T, KAHAN, RA, RB>(acc, cmp, va0, wb0);
+            outer_acc<T, KAHAN, RA, RB>(acc, cmp, va1, wb1);
+        }
+        if (r < rows) {
             T va[RA], wb[RB];
-            ld_vec<T, RA>(sv + r * MPs + ia * RA, va);
-            ld_vec<T, RB>(sw + r * KPs + ib * RB, wb);
-#pragma unroll
-            for (int i = 0; i < RA; ++i)
-#pragma unroll
-                for (int j = 0; j < RB; ++j) {
-                    const int x = i * RB + j;
-                    if constexpr (KAHAN) {
-                        // Kahan's compensated summation: cmp carries the
-                        // low-order part lost by the last addition
-                        const T yv = va[i] * wb[j] - cmp[x];
-                        const T tv = acc[x] + yv;
-                        cmp[x] = (tv - acc[x]) - yv;
-                        acc[x] = tv;
-                    } else {
-                        acc[x] = fma(va[i], wb[j], acc[x]);
-                    }
-                }
+            ld_vec<T, RA>(pv, va);
+            ld_vec<T, RB>(pw, wb);
+            outer_acc<T, KAHAN, RA, RB>(acc, cmp, va, wb);
         }
         __syncthreads();
     }
-    // row groups inside a warp (lanes l, l + L, ...): fixed xor tree
-    Comp cs[RR];
-#pragma unroll
-    for (int x = 0; x < RR; ++x) cs[x] = Comp{(double)acc[x], KAHAN ? -(double)cmp[x] : 0.0};
-#pragma unroll
-    for (int off = L; off < 32; off <<= 1)
-#pragma unroll
-        for (int x = 0; x < RR; ++x) {
-            const Comp o{__shfl_xor_sync(0xffffffffu, cs[x].s, off), __shfl_xor_sync(0xffffffffu, cs[x].c, off)};
-            if constexpr (KAHAN)
-                cs[x] = comp_merge(cs[x], o);
-            else
-                cs[x].s += o.s;
-        }
-    // the block's warps in order, into shared memory (reusing the tiles)
+    // Reduction, four outputs at a time (few registers live): the row groups
+    // inside a warp (lanes l, l + L, ...) by a fixed xor tree, then the
+    // block's warps in order, into shared memory (reusing the tiles).
     Comp *red = reinterpret_cast<Comp *>(tsm_smem);
     const int warp = t >> 5, lane = t & 31;
-    for (int w = 0; w < kTsmThreads / 32; ++w) {
-        if (warp == w && lane < L) {
 #pragma unroll
-            for (int x = 0; x < RR; ++x) {
-                Comp &d = red[lane * RR + x];
-                if (w == 0)
-                    d = cs[x];
-                else if (KAHAN)
-                    d = comp_merge(d, cs[x]);
+    for (int x0 = 0; x0 < RR; x0 += 4) {
+        Comp cs[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cs[q] = Comp{(double)acc[x0 + q], KAHAN ? -(double)cmp[x0 + q] : 0.0};
+#pragma unroll
+        for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const Comp o{__shfl_xor_sync(0xffffffffu, cs[q].s, off), __shfl_xor_sync(0xffffffffu, cs[q].c, off)};
+                if constexpr (KAHAN)
+                    cs[q] = comp_merge(cs[q], o);
                 else
-                    d.s += cs[x].s;
+                    cs[q].s += o.s;
             }
+        for (int w = 0; w < kTsmThreads / 32; ++w) {
+            if (warp == w && lane < L) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Comp &d = red[lane * RR + x0 + q];
+                    if (w == 0)
+                        d = cs[q];
+                    else if (KAHAN)
+                        d = comp_merge(d, cs[q]);
+                    else
+                        d.s += cs[q].s;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     const int nb = gridDim.x;
     for (int o = t; o < L * RR; o += kTsmThreads) {
@@ -297,7 +335,7 @@ __global__ void __launch_bounds__(kTsmThreads) k_tsmm_tile(const T *__restrict__
 #pragma unroll
         for (int j = 0; j < RB; ++j) xr[a][j] = (a < m && b0 + j < k) ? X[(int64_t)a * ldx + b0 + j] : T(0);
     const int stage_elems = tr * MPs;
-    for (int e = t; e < kTsmStages * stage_elems; e += kTsmThreads)
+    for (int e = t; e < 2 * stage_elems; e += kTsmThreads)
         if ((e % MPs) >= m) st[e] = T(0);  // padding columns: zeros (0 x 0 in the products)
     const int64_t ntiles = (n + tr - 1) / tr;
     const int64_t tile0 = (int64_t)blockIdx.x * tiles_per_block;
@@ -306,17 +344,18 @@ __global__ void __launch_bounds__(kTsmThreads) k_tsmm_tile(const T *__restrict__
         const int64_t r0 = tile * tr;
         const int rows = (int)(n - r0 < tr ? n - r0 : tr);
         stage_rows(st + s * stage_elems, MPs, V, ldv, r0, rows, m, vec != 0);
+        cp_async_commit();
     };
-#pragma unroll
-    for (int i = 0; i < kTsmStages - 1; ++i) {
-        if (tile0 + i < tile1) stage(tile0 + i, i);
-        cp_async_commit();
-    }
+    // two tiles: the copy of tile i + 1 overlaps the products of tile i
+    if (tile0 < tile1) stage(tile0, 0);
     for (int64_t tile = tile0; tile < tile1; ++tile) {
-        const int it = (int)(tile - tile0), s = it % kTsmStages;
-        if (tile + kTsmStages - 1 < tile1) stage(tile + kTsmStages - 1, (it + kTsmStages - 1) % kTsmStages);
-        cp_async_commit();
-        cp_async_wait<kTsmStages - 1>();
+        const int s = (int)((tile - tile0) & 1);
+        if (tile + 1 < tile1) {
+            stage(tile + 1, s ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();  // the tile of V is in shared memory before W (which may be V) is written
         const T *sv = st + s * stage_elems;
         const int64_t r0 = tile * tr;
@@ -415,7 +454,7 @@ static int run_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double al
     int lbs = 0;
     while ((1 << lbs) * RB < k) ++lbs;
     const int tr = tile_rows(MPs * (int)sizeof(T));
-    const size_t smem = (size_t)kTsmStages * tr * MPs * sizeof(T);
+    const size_t smem = (size_t)2 * tr * MPs * sizeof(T);
     const int64_t ntiles = std::max<int64_t>(1, (n + tr - 1) / tr);
     if (smem > kTsmSmemMax) return SP_ERR_UNSUPPORTED;
     auto kern = k_tsmm_tile<T, MP, RB>;
