@@ -264,7 +264,14 @@ SP_API int sp_mat_permute(const sp_mat *A, sp_dense *out, const sp_dense *in, in
  *   sp_tsmm      W <- alpha V X + beta W; W may be V itself (in place, then
  *                k = m); any other overlap of W with V or X is SP_ERR_ARG.
  *                beta = 0: W is not read.
- * SP_ERR_UNSUPPORTED for m or k above 32.  Asynchronous on the stream.
+ * Errors: SP_ERR_ARG for a missing or column-major block, m or k below 1;
+ * SP_ERR_DIM for mismatched shapes; SP_ERR_DTYPE for mixed or unsupported
+ * dtypes; SP_ERR_UNSUPPORTED for m or k above 32.  Precision: products and
+ * per-thread sums in the blocks' dtype, the sums of threads and blocks in
+ * float64 ((sum, compensation) pairs for the Kahan variant).  sp_tsmttsm
+ * takes 16 * m * k bytes per thread block (a few hundred blocks) for its
+ * block sums, stream-ordered from the device's default memory pool, and
+ * gives it back on the stream.  Asynchronous on the stream.
  */
 SP_API int sp_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, double beta, int kahan,
                       void *stream);
