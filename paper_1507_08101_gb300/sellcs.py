@@ -443,16 +443,14 @@ def tsmttsm(X, V, W, alpha=1.0, beta=0.0, kahan=False, stream=None):
 def tsmm(W, V, X, alpha=1.0, beta=0.0, stream=None):
     """W <- alpha V X + beta W (sp_tsmm; W may be V); CUDA tensors, row-major."""
     L = lib()
-    hw = sp_dense_view(W)
-    hv = hw if V.data_ptr() == W.data_ptr() else sp_dense_view(V)
-    hx = sp_dense_view(X)
+    # separate views even when V is W: the library recognises the in-place
+    # form by the shared storage and checks that the shapes agree
+    hw, hv, hx = sp_dense_view(W), sp_dense_view(V), sp_dense_view(X)
     try:
         check(L.sp_tsmm(hw, hv, hx, float(alpha), float(beta), _stream(stream)), "sp_tsmm")
     finally:
-        L.sp_dense_destroy(hw, None)
-        if hv is not hw:
-            L.sp_dense_destroy(hv, None)
-        L.sp_dense_destroy(hx, None)
+        for h in (hw, hv, hx):
+            L.sp_dense_destroy(h, None)
     return W
 
 
