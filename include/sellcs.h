@@ -17,8 +17,12 @@
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Compute calls are asynchronous on that stream.  Calls that return sizes to
  *    the host (create, export, info) synchronise the stream.
- *  - Device memory for matrices is allocated by the library (stream-ordered)
- *    and freed by the matching destroy.  Block vectors are either allocated by
+ *  - Device memory for matrices and library-owned block vectors is allocated
+ *    by the library with cudaMalloc (which may synchronise the device; the
+ *    create calls synchronise their stream anyway) and freed by the matching
+ *    destroy, after that call has synchronised its stream.  Temporaries of the
+ *    compute calls (partial sums, host-dot buffers) are stream-ordered
+ *    (cudaMallocAsync / cudaFreeAsync on the call's stream).  Block vectors are either allocated by
  *    the library (sp_dense_create) or are views of caller memory
  *    (sp_dense_view), which the library never frees.
  *  - Block vectors (x, y, z) are always in the caller's original row order;
@@ -163,7 +167,7 @@ SP_API int sp_mat_export_sell_transpose(const sp_mat *A, int64_t *chunkptr, int3
  * val double[nnz].  Synchronises the stream. */
 SP_API int sp_mat_to_csr(const sp_mat *A, int64_t *rowptr, int32_t *col, double *val, void *stream);
 
-/* Frees the device arrays (stream-ordered on the given stream). */
+/* Synchronises the given stream, then frees the device arrays. */
 SP_API int sp_mat_destroy(sp_mat *A, void *stream);
 
 /* ------------------------------------------------------------------ dense block vectors */
@@ -202,6 +206,12 @@ SP_API int sp_dense_destroy(sp_dense *d, void *stream);
 #define SP_SPMV_DOT_ANY (SP_SPMV_DOT_YY | SP_SPMV_DOT_XY | SP_SPMV_DOT_XX)
 
 #define SP_MAX_VSHIFT 1024 /* widest block with per-vector shifts */
+/* With float32 vectors a lane adds its dot-product terms in float over at most
+ * SP_DOT_RUN_F32 of its rows; those float sums then go through a float tree of
+ * at most 5 additions across the lanes of a column and into float64, in which
+ * every later stage adds.  So every term passes through at most
+ * SP_DOT_RUN_F32 + 5 float additions. */
+#define SP_DOT_RUN_F32 32
 
 typedef struct {
     uint32_t flags;
@@ -219,8 +229,9 @@ typedef struct {
  *   x   ncols(A) x w, y (and z) nrows(A) x w; same dtype; row- or column-major
  *   Precision pairs (values / vectors): f64/f64 (f64 accumulation);
  *   f32/f64, bf16/f64, f32/f32, bf16/f32 (f32 accumulation of the row sums;
- *   the epilogue runs in the vector precision).  Dot products are always
- *   accumulated and returned in double.
+ *   the epilogue runs in the vector precision).  Dot products are returned
+ *   in double; they are accumulated in double for f64 vectors, and for f32
+ *   vectors in float over short runs of rows (SP_DOT_RUN_F32), then double.
  *   SHIFT, VSHIFT, DOT_XY and DOT_XX need a square A.  SHIFT and VSHIFT are
  *   exclusive.  x must not overlap y or z, and z must not overlap y
  *   (SP_ERR_ARG).  The reductions are deterministic (fixed order).
@@ -436,6 +447,11 @@ SP_API int sp_cg_destroy(sp_cg *cg, void *stream);
  * first call before any stream capture.  Every call clears the ticket and
  * shares the array, so calls that overlap on the GPU (different streams, no
  * ordering) race and must not be issued.  Asynchronous on `stream`.
+ * Speed: the call has no chunk lengths and no precomputed work partition, so
+ * it runs the per-lane row loop over a block-strided assignment of rows to
+ * warps.  On matrices whose row lengths vary widely (sorted windows, power-law
+ * rows) that is slower than sp_spmv on a matrix handle, which balances the
+ * warps' work and steps float64 chunks in lockstep.
  */
 #define SP_NOALLOC_MAX_W 32
 #define SP_NOALLOC_MAX_BLOCKS 2048
@@ -448,6 +464,15 @@ SP_API int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_t *c
 /* ------------------------------------------------------------------ device info */
 /* Streaming multiprocessor count of the current device (for grid sizing tests). */
 SP_API int sp_device_sm_count(int *count);
+/* Float64 fused multiply-add rate of the current device, measured (no
+ * counterpart in the paper; the float64 products here are bound by that rate on
+ * GB300, so their roofline needs the measured figure): every SM runs 2048
+ * threads of 8 independent chains a <- fma(a, b, c) for 16384 steps; the best of
+ * three timed launches (CUDA events, after one warm-up launch) gives
+ * *tflops = 2 x fused multiply-adds / time in TFLOP/s and *ms its duration
+ * (ms may be NULL).  Synchronises the stream; allocates 8 bytes
+ * stream-ordered. */
+SP_API int sp_device_fp64_rate(double *tflops, double *ms, void *stream);
 
 #ifdef __cplusplus
 }

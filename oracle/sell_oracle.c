@@ -18,7 +18,7 @@
  *  - Transposed product and the sampled product over the pattern (the
  *    derivatives of y = A x with respect to x and to the stored values).
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent:
  *  - the sort is by row length DESCENDING and STABLE (ties keep the original
  *    row order); windows start at row 0, the last one may be short;
  *  - only rows are permuted: column indices and x, y, z stay in the caller's

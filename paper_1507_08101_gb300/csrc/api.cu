@@ -16,6 +16,10 @@ int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t 
 
 static thread_local char g_detail[512] = "";
 
+void sp_internal_set_detail(const char *prefix, const char *why) {
+    snprintf(g_detail, sizeof(g_detail), "%s: %s", prefix, why);
+}
+
 void sp_internal_note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
     snprintf(g_detail, sizeof(g_detail), "%s (%d) in %s at %s:%d", cudaGetErrorString(e), (int)e, what, file,
              line);
@@ -209,8 +213,11 @@ int sp_mat_create_csr(sp_mat **out, int64_t nrows, int64_t ncols, const int64_t 
     bool f32 = flags & SP_MAT_VAL_F32;
     size_t vs = f32 ? 4 : 8;
     int64_t nnz = 0;
-    if (on_dev)
-        SP_CUDA(cudaMemcpy(&nnz, rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (on_dev) {
+        // on the caller's stream, so that a row pointer array written there is complete
+        SP_CUDA(cudaMemcpyAsync(&nnz, rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+    }
     else
         nnz = rowptr[nrows];
     if (nnz < 0) return SP_ERR_FORMAT;

@@ -25,6 +25,8 @@
     } while (0)
 
 void sp_internal_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// Records "prefix: why" as the calling thread's sp_last_error_detail().
+void sp_internal_set_detail(const char *prefix, const char *why);
 
 namespace sp {
 

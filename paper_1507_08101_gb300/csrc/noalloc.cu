@@ -12,6 +12,8 @@
 // kernel as sp_spmv.
 #include <stdio.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "spmv_kernel.cuh"
 
@@ -28,17 +30,21 @@ static __device__ __align__(256) double g_noalloc_partials[3 * SP_NOALLOC_MAX_W 
 static __device__ __align__(256) unsigned g_noalloc_ticket[64];
 
 namespace {
-// Device addresses of the arrays above, looked up once per device.
+// Device addresses of the arrays above, looked up once per device under a
+// mutex, so that two host threads making their first call on one device at
+// the same time both see a complete pair.
 struct NoAllocAddr {
     double *partials = nullptr;
     unsigned *ticket = nullptr;
 };
 NoAllocAddr g_addr[64];
+std::mutex g_addr_mutex;
 
-int noalloc_setup(NoAllocAddr **out) {
+int noalloc_setup(NoAllocAddr *out) {
     int dev = 0;
     SP_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SP_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_addr_mutex);
     NoAllocAddr &a = g_addr[dev];
     if (!a.partials) {
         void *p = nullptr, *t = nullptr;
@@ -47,14 +53,13 @@ int noalloc_setup(NoAllocAddr **out) {
         a.ticket = (unsigned *)t;
         a.partials = (double *)p;
     }
-    *out = &a;
+    *out = a;
     return SP_OK;
 }
 
-// Record why a call was rejected in the thread's error-detail buffer (the
-// writable buffer behind sp_last_error_detail) and return the code.
+// Record why a call was rejected (the thread's sp_last_error_detail) and return the code.
 int noalloc_reject(int code, const char *why) {
-    snprintf(const_cast<char *>(sp_last_error_detail()), 512, "sp_spmv_noalloc: %s", why);
+    sp_internal_set_detail("sp_spmv_noalloc", why);
     return code;
 }
 }  // namespace
@@ -88,11 +93,11 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     if (nrows > 0 && (!val || !col || !chunkptr || !slotlen || !x || !y))
         return noalloc_reject(SP_ERR_ARG, "null matrix or vector pointer");
 
-    NoAllocAddr *na = nullptr;
+    NoAllocAddr na;
     SP_TRY(noalloc_setup(&na));
     cudaStream_t s = (cudaStream_t)stream;
     // the ticket must start at zero; a call that did not finish could have left it set
-    SP_CUDA(cudaMemsetAsync(na->ticket, 0, sizeof(unsigned), s));
+    SP_CUDA(cudaMemsetAsync(na.ticket, 0, sizeof(unsigned), s));
 
     const int64_t nchunks = (nrows + C - 1) / C;
     SpmvArgs a{};
@@ -123,8 +128,8 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     a.dot = dot;
     a.dot_stride = w;
     a.dot_off = 0;
-    a.partials = na->partials;
-    a.ticket = na->ticket;
+    a.partials = na.partials;
+    a.ticket = na.ticket;
     a.sched = nullptr;
     a.sched_rounds = 0;
     a.wbounds = nullptr;

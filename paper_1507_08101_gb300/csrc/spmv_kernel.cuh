@@ -279,6 +279,9 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
 #ifndef SP_LOCKSTEP
 #define SP_LOCKSTEP 1
 #endif
+// Longest run of row iterations over which a lane of a float32-vector product
+// accumulates its dot products in float (SP_DOT_RUN_F32, defined in the header).
+static_assert(SP_DOT_RUN_F32 >= 1, "dot run length");
 #ifndef SP_LS_SPREAD
 #define SP_LS_SPREAD 0.3
 #endif
@@ -393,12 +396,21 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
     }
 }
 
+// Per-warp float64 sums of the dot products in shared memory: the warp's
+// running bank while it works (float32 vectors, see k_spmmv), then the input of
+// the block-level reduction.
+__device__ __forceinline__ double (*dot_smem())[3][kMaxTileW] {
+    __shared__ double sred[kMainWarps][3][kMaxTileW];
+    return sred;
+}
+
 // Final step of the fused reductions: per-block partial sums, and the last
-// block to arrive adds them up in block order.
-template <int CPL, int G, int DM>
+// block to arrive adds them up in block order.  BANKED: the warp's sums so far
+// are already in its row of dot_smem() and this call adds to them.
+template <int CPL, int G, int DM, bool BANKED>
 __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&dyy)[CPL], double (&dxy)[CPL],
                                             double (&dxx)[CPL]) {
-    __shared__ double sred[kMainWarps][3][kMaxTileW];
+    double (*sred)[3][kMaxTileW] = dot_smem();
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -415,9 +427,15 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
         for (int c = 0; c < CPL; ++c) {
             int k = k0 + c;
             if (k < a.w) {
-                sred[warp][0][k] = dyy[c];
-                sred[warp][1][k] = dxy[c];
-                sred[warp][2][k] = dxx[c];
+                if constexpr (BANKED) {
+                    sred[warp][0][k] += dyy[c];
+                    sred[warp][1][k] += dxy[c];
+                    sred[warp][2][k] += dxx[c];
+                } else {
+                    sred[warp][0][k] = dyy[c];
+                    sred[warp][1][k] = dxy[c];
+                    sred[warp][2][k] = dxx[c];
+                }
             }
         }
     }
@@ -485,10 +503,14 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
     // dot accumulators per lane: float64 for float64 vectors; for float32
-    // vectors float per lane (a few tens of rows each), float64 from the
-    // warp reduction on, so the kernel spends no float64 instruction per row
+    // vectors float per lane over at most SP_DOT_RUN_F32 row iterations of the
+    // warp, then a float xor tree across the lanes of each column and a float64
+    // add into the warp's bank in shared memory (dot_flush), so the kernel
+    // spends no float64 instruction per row and every term passes through at
+    // most SP_DOT_RUN_F32 + 5 float additions
     using DT = typename std::conditional<sizeof(XT) == 8, double, float>::type;
     constexpr bool DOTS = DM != 0;
+    constexpr bool BANK = DOTS && sizeof(XT) == 4;
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
     constexpr int R = 32 / G;
@@ -527,6 +549,40 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     }
 
     const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
+
+    if constexpr (BANK) {
+        double (*bank)[3][kMaxTileW] = dot_smem();
+        for (int t = lane; t < 3 * kMaxTileW; t += 32) bank[warp][t / kMaxTileW][t % kMaxTileW] = 0.0;
+        __syncwarp();
+    }
+    // Called by every lane of the warp at the same points (once per uniform
+    // iteration of the slot loops): after SP_DOT_RUN_F32 iterations the float
+    // sums move into the warp's float64 bank.
+    int dot_iters = 0;
+    auto dot_tick = [&]() {
+        if constexpr (BANK) {
+            if (++dot_iters < SP_DOT_RUN_F32) return;
+            dot_iters = 0;
+            double (*bank)[3][kMaxTileW] = dot_smem();
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+                for (int o = G; o < 32; o <<= 1) {
+                    if constexpr ((DM & 1) != 0) dyy[c] += __shfl_xor_sync(0xffffffffu, dyy[c], o);
+                    if constexpr ((DM & 2) != 0) dxy[c] += __shfl_xor_sync(0xffffffffu, dxy[c], o);
+                    if constexpr ((DM & 4) != 0) dxx[c] += __shfl_xor_sync(0xffffffffu, dxx[c], o);
+                }
+                if (lane < G && k0 + c < a.w) {
+                    if constexpr ((DM & 1) != 0) bank[warp][0][k0 + c] += (double)dyy[c];
+                    if constexpr ((DM & 2) != 0) bank[warp][1][k0 + c] += (double)dxy[c];
+                    if constexpr ((DM & 4) != 0) bank[warp][2][k0 + c] += (double)dxx[c];
+                }
+                if constexpr ((DM & 1) != 0) dyy[c] = DT(0);
+                if constexpr ((DM & 2) != 0) dxy[c] = DT(0);
+                if constexpr ((DM & 4) != 0) dxx[c] = DT(0);
+            }
+        }
+    };
 
     // one row slot: row sums, then y = alpha (t - gamma x_i) + beta y_i, dots, chain
     // Where a slot's row lives: its original row i (-1 for a padding row),
@@ -631,7 +687,15 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             if (kb >= 0) {
                 const int64_t s0 = (int64_t)kb * 32;
                 const int64_t s1 = s0 + 32 < a.nslots ? s0 + 32 : a.nslots;
-                for (int64_t s = s0 + rw; s < s1; s += Rr) slot(meta_of(s));
+                if constexpr (BANK) {
+                    // every lane runs the same iterations (dot_tick is warp-wide)
+                    for (int64_t sb = s0; sb < s1; sb += Rr) {
+                        if (sb + rw < s1) slot(meta_of(sb + rw));
+                        dot_tick();
+                    }
+                } else {
+                    for (int64_t s = s0 + rw; s < s1; s += Rr) slot(meta_of(s));
+                }
             }
             kb = knext;
         }
@@ -648,8 +712,19 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         const int64_t s1e = (int64_t)a.wbounds[gw + 1] * 32;
         const int64_t s1 = s1e < a.nslots ? s1e : a.nslots;
         int64_t s = s0 + rw;
-        if (prefetch_meta) {
-            // the next slot's metadata is loaded while this slot is computed
+        if (prefetch_meta && BANK) {
+            // the next slot's metadata is loaded while this slot is computed;
+            // the loop runs the same iterations in every lane (dot_tick is warp-wide)
+            Meta cur{-1, 0, 0, -1};
+            if (s < s1) cur = meta_of(s);
+            for (int64_t sb = s0; sb < s1; sb += Rr, s += Rr) {
+                Meta nxt{-1, 0, 0, -1};
+                if (s + Rr < s1) nxt = meta_of(s + Rr);
+                slot(cur);
+                dot_tick();
+                cur = nxt;
+            }
+        } else if (prefetch_meta) {
             Meta cur{-1, 0, 0, -1};
             if (s < s1) cur = meta_of(s);
             for (; s < s1; s += Rr) {
@@ -657,6 +732,11 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
                 if (s + Rr < s1) nxt = meta_of(s + Rr);
                 slot(cur);
                 cur = nxt;
+            }
+        } else if constexpr (BANK) {
+            for (int64_t sb = s0; sb < s1; sb += Rr, s += Rr) {
+                if (s < s1) slot(meta_of(s));
+                dot_tick();
             }
         } else {
             for (; s < s1; s += Rr) slot(meta_of(s));
@@ -666,6 +746,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         for (int64_t base = (int64_t)blockIdx.x * rows; base < a.nslots; base += (int64_t)gridDim.x * rows) {
             const int64_t s = base + warp * Rr + rw;
             if (s < a.nslots) slot(meta_of(s));
+            dot_tick();
         }
     }
     if constexpr (DOTS) {
@@ -676,7 +757,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             vxy[c] = (DM & 2) ? (double)dxy[(DM & 2) ? c : 0] : 0.0;
             vxx[c] = (DM & 4) ? (double)dxx[(DM & 4) ? c : 0] : 0.0;
         }
-        reduce_dots<CPL, G, DM>(a, k0, vyy, vxy, vxx);
+        reduce_dots<CPL, G, DM, BANK>(a, k0, vyy, vxy, vxx);
     }
 }
 

@@ -319,7 +319,7 @@ __global__ void k_tsmttsm_final(const Comp *__restrict__ part, int nb, int m, in
 // Lanes per row LB = 2^lbs cover the k outputs of a row in slices of RB; the
 // 256 / LB rows a block works on at once are the row groups.
 template <class T, int MP, int RB>
-__global__ void __launch_bounds__(kTsmThreads) k_tsmm_tile(const T *__restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kTsmThreads) k_tsmm_tile(const T *V, int64_t ldv,
                                                            const T *__restrict__ X, int64_t ldx, T *W, int64_t ldw,
                                                            int64_t n, int m, int k, int lbs, int tr,
                                                            int64_t tiles_per_block, int vec, T alpha, T beta) {

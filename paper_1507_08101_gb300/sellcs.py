@@ -63,7 +63,9 @@ class sp_cg_stats_t(ct.Structure):
 
 
 SP_BATCH_MAX_W = 8
+SP_MAX_VSHIFT = 1024
 SP_NOALLOC_MAX_W = 32
+SP_DOT_RUN_F32 = 32  # float32-vector dots: longest float run of rows per lane
 
 
 class SpError(RuntimeError):
@@ -84,6 +86,7 @@ _SIGS = {
     "sp_error_string": (ct.c_char_p, [I]),
     "sp_last_error_detail": (ct.c_char_p, []),
     "sp_device_sm_count": (I, [ct.POINTER(I)]),
+    "sp_device_fp64_rate": (I, [ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), P]),
     "sp_mat_create_csr": (I, [PP, I64, I64, P, P, P, I, I64, I, U, P]),
     "sp_mat_update_values": (I, [P, P, U, P]),
     "sp_mat_clone_values": (I, [PP, P, I, P]),
@@ -142,6 +145,13 @@ def lib():
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def device_fp64_rate(stream=None):
+    """(TFLOP/s, ms) of the float64 fused multiply-add micro-benchmark."""
+    t, ms = ct.c_double(), ct.c_double()
+    check(lib().sp_device_fp64_rate(ct.byref(t), ct.byref(ms), _stream(stream)), "sp_device_fp64_rate")
+    return t.value, ms.value
 
 
 def sp_error_string(code: int) -> str:

@@ -16,6 +16,19 @@ So, per entry, |y_gpu - y| <= tol * s with s = |alpha|(|A||x|) +
 where the oracle is given exactly the values the GPU stores (rounded to f32 or
 bf16), so the storage rounding is not part of this comparison and is reported
 separately against the unrounded float64 matrix.
+
+Dot products (dot_bound): the GPU sums terms of its own y, so its result D^
+differs from the oracle's D (terms of the oracle's y) by
+  (1) the propagated error of y: with e_i = tol * s_i the bound on |y^_i - y_i|,
+      |sum y^_i^2 - sum y_i^2| <= sum e_i (2|y_i| + e_i) and
+      |sum x_i y^_i - sum x_i y_i| <= sum |x_i| e_i  (x is exact on both sides);
+  (2) the accumulation error: a sum in which every term passes through at most
+      n additions in a format of unit roundoff u is off by at most
+      gamma_n = n u / (1 - n u) times the sum of the terms' magnitudes.  Float32
+      vectors add in float over at most SP_DOT_RUN_F32 rows per lane plus a
+      float tree of at most 5 levels (n = SP_DOT_RUN_F32 + 5, u = 2^-24); every
+      later stage (per-warp bank, warp tree, block, grid) adds in float64, and
+      no term passes through more than N + 2100 of those (u = 2^-53).
 """
 import numpy as np
 import torch
@@ -30,6 +43,33 @@ def tol_for(vdt: str, xdt: str, maxlen: int) -> float:
     if vdt == "f64" and xdt == "f64":
         return 1e-12
     return 1.1 * (maxlen + 6) * U32
+
+
+U53 = 2.0 ** -53
+
+
+def gamma(n, u):
+    return n * u / (1 - n * u)
+
+
+def dot_bound(name, yr, X, e, xdt, N):
+    """Bound on |dot_gpu - dot_oracle| per column (derivation in the module
+    docstring).  yr: oracle y (N x w), X: x as both sides use it, e: per-entry
+    bound on |y_gpu - y_oracle| (N x w)."""
+    g = gamma(N + 2100, U53) + 1e-15  # float64 stages + the oracle's own rounding
+    if xdt == "f32":
+        g += gamma(sellcs.SP_DOT_RUN_F32 + 5, U32)
+    xa = np.abs(X[:N])
+    if name == "dot_yy":
+        prop = e * (2 * np.abs(yr) + e)
+        terms = yr * yr + prop
+    elif name == "dot_xy":
+        prop = xa * e
+        terms = xa * (np.abs(yr) + e)
+    else:
+        prop = np.zeros_like(xa)
+        terms = xa * xa
+    return prop.sum(0) + g * terms.sum(0)
 
 
 def to_dev(a, dtype=torch.float64):
@@ -116,25 +156,12 @@ def run_case(A, C, sigma, w, flags, *, vdt="f64", xdt="f64", layout="row", ld_pa
     if "chain" in flags:
         sz = 0.9 * np.abs(Z0) + 0.1 * (np.abs(yr) + s)
         assert_close(z, zr, sz, tol + (U32 if xdt == "f32" else 0), "z")
-    # dots: against the oracle (scale: sum of |x||y| type terms) and unrequested slots untouched.
-    # Float32 vectors accumulate their dots in float per lane (at most N terms
-    # in one lane), so they add the recursive-summation bound gamma_N of float
-    # over the sum of the terms' magnitudes.
-    xabs = np.abs(X[:N]) if M == N else None
-    gN = N * U32 / (1 - N * U32) if xdt == "f32" else 0.0
+    # dots: against the oracle within dot_bound, and unrequested slots untouched
+    e = tol * s
     for q, name in enumerate(["dot_yy", "dot_xy", "dot_xx"]):
         got = d[q * w:(q + 1) * w]
         if name in flags:
-            if name == "dot_yy":
-                terms = np.abs(yr * yr).sum(0)
-                sc = (2 * np.abs(yr) * s).sum(0) * 2 + terms * 1e-14
-            elif name == "dot_xy":
-                terms = np.abs(xabs * yr).sum(0)
-                sc = (xabs * s).sum(0) * 2 + terms * 1e-14
-            else:
-                terms = (xabs * xabs).sum(0)
-                sc = terms * 1e-13 / tol
-            assert_close(got, dr[q * w:(q + 1) * w], sc + gN * terms / tol, tol, name)
+            assert_close(got, dr[q * w:(q + 1) * w], dot_bound(name, yr, X, e, xdt, N), 1.0, name)
         else:
             assert np.all(np.isnan(got)), f"{name} slot written though not requested"
     return y, yr, mat

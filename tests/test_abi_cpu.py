@@ -37,6 +37,16 @@ def test_every_declared_symbol_is_exported(L):
         assert n in sellcs.exported_symbols(), f"binding lacks {n}"
 
 
+def test_binding_constants_match_header():
+    """Every integer #define of the header that the binding mirrors has the same value there."""
+    from paper_1507_08101_gb300 import sellcs
+    defs = dict(re.findall(r"^#define\s+(SP_\w+)\s+(\d+)\s*(?:/\*.*)?$", open(HEADER).read(), flags=re.M))
+    shared = [n for n in defs if hasattr(sellcs, n)]
+    assert {"SP_DOT_RUN_F32", "SP_NOALLOC_MAX_W", "SP_MAX_VSHIFT"} <= set(shared)
+    for n in shared:
+        assert getattr(sellcs, n) == int(defs[n]), n
+
+
 def test_error_strings(L):
     from paper_1507_08101_gb300 import sellcs
     assert sellcs.sp_error_string(0) == "ok"

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 from paper_1507_08101_gb300 import sellcs
-from tests.gpu_helpers import U32, assert_close, run_case, to_dev
+from tests.gpu_helpers import U32, assert_close, dot_bound, run_case, to_dev
 from workloads import generators as gen
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -52,8 +52,9 @@ def test_irregular_full_augmented(cuda_ok):
     assert_close(z.cpu().numpy(), zr, 0.9 * np.abs(Z0) + 0.1 * s, 1e-12, "z")
     d = dot.cpu().numpy()
     assert np.isnan(d[2])
-    assert abs(d[0] - dr[0]) <= 1e-12 * float((2 * np.abs(yr) * s).sum() * 2)
-    assert abs(d[1] - dr[1]) <= 1e-12 * float((np.abs(X) * s).sum() * 2)
+    e = 1e-12 * s
+    assert abs(d[0] - dr[0]) <= dot_bound("dot_yy", yr, X, e, "f64", A.nrows)[0]
+    assert abs(d[1] - dr[1]) <= dot_bound("dot_xy", yr, X, e, "f64", A.nrows)[0]
     # consistency pin: dots recomputed on the host from the returned y
     assert abs(d[0] - float((yg * yg).sum())) <= 1e-13 * float((yg * yg).sum())
     assert abs(d[1] - float((X * yg).sum())) <= 1e-13 * float(np.abs(X * yg).sum())
@@ -96,6 +97,37 @@ def test_anderson_chebyshev_steps(cuda_ok, anderson, vdt, xdt):
         exact = oracle.spmmv(A, w0h, alpha=1 / a)[0]
         rel = np.abs(w1h - exact).max() / np.abs(exact).max()
         assert rel < (2 ** -8 if vdt == "bf16" else 2 ** -20)
+
+
+@pytest.mark.parametrize("vdt", ["f32", "bf16"])
+def test_anderson_float32_dots_full(cuda_ok, anderson, vdt):
+    """The Anderson workload at full size (N = 2^21, width 16) with float32
+    vectors: one step y = A~ x with <y,y>, <x,y>, <x,x>.  Every entry of y and
+    every column's three dots against the oracle; the dots within dot_bound,
+    whose float part is gamma over SP_DOT_RUN_F32 + 5 additions (the kernel's
+    longest float run per lane plus the float lane tree), not over N."""
+    A, X = anderson
+    a = 1.01 * (6 + 8.25)
+    X = X.astype(np.float32).astype(np.float64)
+    vals = oracle.round_values(A.val, vdt)
+    m = sellcs.SellMatrix(A, C=32, sigma=1, dtype=vdt)
+    x = to_dev(X, torch.float32)
+    y = torch.zeros_like(x)
+    dot = sellcs.spmv(m, x, y, alpha=1 / a, dot_yy=True, dot_xy=True, dot_xx=True)
+    torch.cuda.synchronize()
+    yr, dr, _ = oracle.spmmv(A, X, val=vals, alpha=1 / a, dot_yy=True, dot_xy=True, dot_xx=True)
+    s = oracle.spmmv_scale(A, X, val=vals, alpha=1 / a) + np.abs(yr)
+    tol = 1.1 * 13 * U32
+    assert_close(y.double().cpu().numpy(), yr, s, tol, f"y {vdt}/f32")
+    d = dot.cpu().numpy()
+    w = X.shape[1]
+    for q, name in enumerate(["dot_yy", "dot_xy", "dot_xx"]):
+        bound = dot_bound(name, yr, X, tol * s, "f32", A.nrows)
+        assert_close(d[q * w:(q + 1) * w], dr[q * w:(q + 1) * w], bound, 1.0, f"{name} {vdt}/f32")
+        # the bound is far from vacuous: under 1e-5 of the sum of the terms' magnitudes
+        xa = np.abs(X)
+        mag = {"dot_yy": yr * yr, "dot_xy": xa * np.abs(yr), "dot_xx": xa * xa}[name].sum(0)
+        assert np.all(bound < 1e-5 * mag), (name, float((bound / mag).max()))
 
 
 def test_clean_lattice_plane_waves_chebyshev(cuda_ok):

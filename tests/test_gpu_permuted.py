@@ -1,14 +1,17 @@
 """Permuted space (SP_MAT_PERMUTED_SPACE): vectors in SELL row order, column
 indices stored as slots.  Moving x, y0, z0 into SELL order (sp_mat_permute),
-multiplying, and moving y, z back gives the same bits as the product in the
-user's order (same entries, same order in every row, same slot order of the
-dot accumulation); the CSR export returns the user's matrix."""
+multiplying, and moving y, z back gives y, z and the dots of the oracle's
+augmented product on the user's vectors (within the tolerances of the other
+parity tests), and the same bits as the product in the user's order (same
+entries, same order in every row, same slot order of the dot accumulation);
+the CSR export returns the user's matrix."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1507_08101_gb300 import sellcs
-from tests.gpu_helpers import to_dev
+from tests.gpu_helpers import assert_close, dot_bound, to_dev, tol_for
 from workloads import generators as gen
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +32,10 @@ def test_permuted_space_matches_user_order(cuda_ok, matrix, C, sigma, w, xdt):
     mu = sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=vdt)
     mp = sellcs.SellMatrix(A, C=C, sigma=sigma, dtype=vdt, permuted=True)
     rng = np.random.default_rng(62)
-    X, Y0, Z0 = (to_dev(rng.uniform(-1, 1, (A.nrows, w)), tdt) for _ in range(3))
+    Xh, Y0h, Z0h = (rng.uniform(-1, 1, (A.nrows, w)) for _ in range(3))
+    if xdt == "f32":
+        Xh, Y0h, Z0h = (v.astype(np.float32).astype(np.float64) for v in (Xh, Y0h, Z0h))
+    X, Y0, Z0 = (to_dev(v, tdt) for v in (Xh, Y0h, Z0h))
     kw = dict(alpha=0.5, gamma=0.25, beta=-1.5, dot_yy=True, dot_xy=True, dot_xx=True, delta=0.9, eta=0.1)
     y, z = Y0.clone(), Z0.clone()
     d = sellcs.spmv(mu, X, y, z=z, **kw)
@@ -41,6 +47,24 @@ def test_permuted_space_matches_user_order(cuda_ok, matrix, C, sigma, w, xdt):
     sellcs.mat_permute(mp, yb, yp, False)
     sellcs.mat_permute(mp, zb, zp, False)
     torch.cuda.synchronize()
+    # against the oracle, in the user's order
+    vals = oracle.round_values(A.val, vdt)
+    okw = dict(val=vals, alpha=0.5, gamma=0.25, beta=-1.5, y0=Y0h)
+    yr, dr, zr = oracle.spmmv(A, Xh, **okw, dot_yy=True, dot_xy=True, dot_xx=True, delta=0.9, eta=0.1, z0=Z0h)
+    sc = oracle.spmmv_scale(A, Xh, **okw)
+    tol = tol_for(vdt, xdt, int(np.diff(A.rowptr).max()))
+    if xdt == "f32":
+        sc = sc + np.abs(yr)
+    yg = yb.double().cpu().numpy().reshape(A.nrows, w)
+    assert_close(yg, yr, sc, tol, "permuted-space y vs oracle")
+    zsc = 0.9 * np.abs(Z0h) + 0.1 * (np.abs(yr) + sc)
+    assert_close(zb.double().cpu().numpy().reshape(A.nrows, w), zr, zsc, tol + (2 ** -24 if xdt == "f32" else 0),
+                 "permuted-space z vs oracle")
+    dpn = dp.cpu().numpy()
+    for q, name in enumerate(["dot_yy", "dot_xy", "dot_xx"]):
+        assert_close(dpn[q * w:(q + 1) * w], dr[q * w:(q + 1) * w], dot_bound(name, yr, Xh, tol * sc, xdt, A.nrows),
+                     1.0, f"permuted-space {name} vs oracle")
+    # and the same bits as the user-order product
     assert torch.equal(yb, y) and torch.equal(zb, z)
     assert torch.equal(dp, d)
 
