@@ -164,8 +164,17 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
             AT acc[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+            int bad = 0;
             row_product<VT, XT, AT, CPL, true, U>(val + cur.off, colp + cur.off, (int)C << lt, len_t, xk, w, 1,
-                                                  nvalid, acc);
+                                                  nvalid, acc, bad);
+            if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value) {
+                if (bad) {  // x outside the fast conversion's range: again with the conversion instruction
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+                    row_product<VT, XT, AT, CPL, true, U, true>(val + cur.off, colp + cur.off, (int)C << lt, len_t,
+                                                                xk, w, 1, nvalid, acc, bad);
+                }
+            }
             bool epi = true;
             if (T > 1) {
 #pragma unroll
@@ -179,7 +188,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
                 if (f & SP_SPMV_AXPBY) load_out<XT, CPL, true>((const XT *)Mp->y0 + i * w + k0, 1, nvalid, yo);
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                    XT v = (XT)acc[c];
+                    XT v = acc_to_x<XT, AT>(acc[c]);
                     if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
                     if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
                     t[c] = v;

@@ -1,0 +1,9 @@
+// SpMMV kernel variants with bfloat16 values and float64 vectors (float32 accumulation),
+// padded block widths 8, 16, 32.
+#include "spmv_launch.cuh"
+
+namespace sp {
+SP_INSTANTIATE_WIDTH(__nv_bfloat16, double, 8)
+SP_INSTANTIATE_WIDTH(__nv_bfloat16, double, 16)
+SP_INSTANTIATE_WIDTH(__nv_bfloat16, double, 32)
+}  // namespace sp

@@ -75,6 +75,7 @@ struct SpmvArgs {
     const int32_t *wbounds;  // static partition of this grid (null: block-strided loop)
     int32_t nsm;             // SMs the grid was sized for
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
+    int32_t log2C;           // log2 of C when C is a power of two, else -1
     const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
     double gamma[kMaxTileW];
 };
@@ -147,6 +148,69 @@ __device__ __forceinline__ AT val_to_acc(VT v) { return (AT)v; }
 template <>
 __device__ __forceinline__ float val_to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) {
     return __bfloat162float(v);
+}
+
+// Precision changes between float64 vectors and float32 row sums, written with
+// integer instructions: on GB300 a float64 <-> float32 conversion instruction
+// runs on the float64 pipe, which issues about two lanes per SM and cycle, so
+// one conversion per gathered x element (values in float32 or bfloat16 with
+// float64 vectors) would cost as much as the float64 product it replaces.
+//
+// narrow_fast: float64 -> float32, round to nearest even, bit-identical to the
+// conversion instruction whenever the result is a normal float or a rounded
+// zero (|d| < 2^-150); every other input (results in the float32 subnormal
+// range, overflow, infinities, NaN) sets `bad`, and the caller recomputes
+// with the conversion instruction (x_to_acc<..., true>).
+__device__ __forceinline__ float narrow_fast(double d, int &bad) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned s = hi & 0x80000000u;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    // exponent rebiased by 1023 - 127 = 896 (no borrow for e >= 897), 20 + 3
+    // mantissa bits from hi, 3 from lo; then round on the 29 dropped bits
+    unsigned f = s | (((hi - 0x38000000u) << 3) & 0x7ffffff8u) | (lo >> 29);
+    const unsigned r = lo & 0x1fffffffu;
+    f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    const bool tiny = e <= 872u;                  // |d| < 2^-150 (or zero): rounds to a signed zero
+    const bool normal = e - 897u <= 253u;         // result exponent 1..254 before rounding
+    bad |= (tiny || normal) ? 0 : 1;
+    return __uint_as_float(tiny ? s : f);
+}
+
+// widen_bits: float32 -> float64 (exact) for every input, by integer
+// instructions (normal, zero, subnormal, infinity, NaN with its payload).
+__device__ __forceinline__ double widen_bits(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned s = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi = s | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0u) {
+        // zero, or a subnormal m 2^-149: the leading one moves to bit 23
+        const int sh = __clz(m) - 8;
+        const unsigned mm = (m << (sh & 31)) & 0x7fffffu;
+        hi = m == 0u ? s : (s | ((unsigned)(897 - sh) << 20) | (mm >> 3));
+        lo = m == 0u ? 0u : (mm << 29);
+    }
+    if (e == 255u) hi = s | 0x7ff00000u | (m >> 3);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// A gathered x element in the accumulation precision.  EXACT: the conversion
+// instruction (the recompute path of narrow_fast's rare inputs).
+template <class AT, class XT, bool EXACT>
+__device__ __forceinline__ AT x_to_acc(XT v, int &bad) {
+    if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value && !EXACT)
+        return narrow_fast(v, bad);
+    else
+        return (AT)v;
+}
+
+// A row sum in the vector precision.
+template <class XT, class AT>
+__device__ __forceinline__ XT acc_to_x(AT v) {
+    if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value)
+        return widen_bits(v);
+    else
+        return (XT)v;
 }
 
 // Loads of the matrix stream (values, column indices): read once, so they
@@ -288,10 +352,10 @@ static_assert(SP_DOT_RUN_F32 >= 1, "dot run length");
 #ifndef SP_LS_SPREAD_DOTS
 #define SP_LS_SPREAD_DOTS 0.15
 #endif
-template <class VT, class XT, class AT, int CPL, bool VEC, int U>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false>
 __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                                int len, int clen, const XT *__restrict__ xk, int64_t xrs,
-                                               int64_t xcs, int nvalid, AT (&acc)[CPL]) {
+                                               int64_t xcs, int nvalid, AT (&acc)[CPL], int &bad) {
     int j = 0;
     for (; j + U <= clen; j += U) {
         int32_t cc[U];
@@ -312,7 +376,7 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
                     load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
                     AT v = val_to_acc<AT, VT>(vv[u]);
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
                 }
             }
         }
@@ -334,7 +398,7 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
                     load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
                     AT v = val_to_acc<AT, VT>(vv[u]);
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
                 }
             }
         }
@@ -346,10 +410,10 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
 // (len mod U) entries are issued the same way under a predicate, so a short
 // row (fewer than U entries) costs one round trip, not one per entry.  The
 // products are added in the order j = 0, 1, ..., len - 1 in every case.
-template <class VT, class XT, class AT, int CPL, bool VEC, int U>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false>
 __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                             int len, const XT *__restrict__ xk, int64_t xrs, int64_t xcs,
-                                            int nvalid, AT (&acc)[CPL]) {
+                                            int nvalid, AT (&acc)[CPL], int &bad) {
     int j = 0;
     for (; j + U <= len; j += U) {
         int32_t cc[U];
@@ -368,7 +432,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
                 load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
                 AT v = val_to_acc<AT, VT>(vv[u]);
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
             }
         }
     }
@@ -389,7 +453,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
                     load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
                     AT v = val_to_acc<AT, VT>(vv[u]);
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, (AT)xv[c], acc[c]);
+                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
                 }
             }
         }
@@ -498,7 +562,14 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 // DM: the dot products compiled in (bit 0 <y,y>, bit 1 <x,y>, bit 2 <x,x>);
 // the launcher uses 0, 3 (the pair of the bench product and of the KPM steps)
 // or 7, and the flags pick which of them are written.
-template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS>
+// EPI: the epilogue's arithmetic, fixed at compile time where the float64
+// pipe binds (float64 vectors without dots): 0 y = t; 1 y = alpha t + beta y
+// (the Chebyshev step); 2 every augmentation by its runtime flag.  A runtime
+// flag that is off still costs: the compiler turns a short conditional into
+// an unconditional operation and a select, and for float64 vectors that
+// operation occupies the float64 pipe (Laplacian 256^3: three of every eleven
+// float64 instructions per row were such).
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
@@ -529,8 +600,12 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     const int k0 = gl * CPL;
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const uint32_t f = a.flags;
-    const bool shift = (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0;
-    const bool need_xi = shift || (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX));
+    static_assert(EPI == 2 || DM == 0, "compile-time epilogues have no dots");
+    const bool shift = EPI == 2 && (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0;
+    const bool do_scale = EPI == 2 ? (f & SP_SPMV_SCALE) != 0 : EPI == 1;
+    const bool do_axpby = EPI == 2 ? (f & SP_SPMV_AXPBY) != 0 : EPI == 1;
+    const bool do_chain = EPI == 2 && (f & SP_SPMV_CHAIN_AXPBY) != 0;
+    const bool need_xi = shift || (DM != 0 && (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX)));
     const VT *__restrict__ val = (const VT *)a.val;
     const XT *__restrict__ x = (const XT *)a.x;
     XT *y = (XT *)a.y;
@@ -594,7 +669,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     auto meta_of = [&](int64_t s) {
         Meta m;
         m.i = a.perm ? (int64_t)a.perm[s] : (s < a.nrows ? s : -1);
-        const uint32_t cidx = (uint32_t)s / (uint32_t)a.C;
+        const uint32_t cidx = a.log2C >= 0 ? (uint32_t)s >> a.log2C : (uint32_t)s / (uint32_t)a.C;
         m.off = a.chunkptr[cidx] + (int64_t)((uint32_t)s - cidx * (uint32_t)a.C);
         m.len = a.slotlen[s];
         // without chunk lengths each lane runs to its own length (same sums)
@@ -613,7 +688,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         XT *yp = y + i * a.yrs + (int64_t)k0 * a.ycs;
         if (early_epi && epi_lane) {
             if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
-            if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+            if (do_axpby) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
         }
         const int len_t = len > tt ? (len - tt + T - 1) >> lt : 0;
         XT rs[CPL];  // the row sums, in the vector precision
@@ -621,13 +696,25 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             AT acc[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+            int bad = 0;
             if constexpr (LS)
                 row_product_ls<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
                                                         a.C << lt, len_t, (m.clen + T - 1) >> lt, xk, a.xrs, a.xcs,
-                                                        nvalid, acc);
+                                                        nvalid, acc, bad);
             else
                 row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                                     a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc);
+                                                     a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc, bad);
+            if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value) {
+                // an x element outside the fast conversion's range: this lane's
+                // share of the row again, with the conversion instruction
+                if (bad) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
+                    row_product<VT, XT, AT, CPL, VEC, U, true>(val + off + (int64_t)tt * a.C,
+                                                               a.col + off + (int64_t)tt * a.C, a.C << lt, len_t, xk,
+                                                               a.xrs, a.xcs, nvalid, acc, bad);
+                }
+            }
             if (MT && T > 1) {
                 // combine the T partial sums of the row (fixed xor tree)
 #pragma unroll
@@ -636,19 +723,19 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
                 if (tt != 0) return;
             }
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) rs[c] = (XT)acc[c];
+            for (int c = 0; c < CPL; ++c) rs[c] = acc_to_x<XT, AT>(acc[c]);
         }
         if (nvalid <= 0) return;
         if (!early_epi) {
             if (need_xi) load_cols<XT, CPL, VEC>(xk + i * a.xrs, a.xcs, nvalid, xi);
-            if (f & SP_SPMV_AXPBY) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
+            if (do_axpby) load_out<XT, CPL, VEC>(yp, a.ycs, nvalid, yo);
         }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             XT v = rs[c];
             if (shift) v = fma_rn(-gam[c], xi[c], v);
-            if (f & SP_SPMV_SCALE) v = mul_rn(alpha, v);
-            if (f & SP_SPMV_AXPBY) v = fma_rn(beta, yo[c], v);
+            if (do_scale) v = mul_rn(alpha, v);
+            if (do_axpby) v = fma_rn(beta, yo[c], v);
             t[c] = v;
         }
         store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
@@ -666,7 +753,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
                 }
             }
         }
-        if (f & SP_SPMV_CHAIN_AXPBY) {
+        if (do_chain) {
             XT zo[CPL];
             XT *zp = z + i * a.zrs + (int64_t)k0 * a.zcs;
             load_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);

@@ -1,5 +1,5 @@
-// Width dispatch for the SpMMV kernel; included by the per-precision
-// translation units (spmv_f64.cu, spmv_f32.cu, spmv_bf16.cu), which compile in
+// Launch of the SpMMV kernel variants; included by the per-precision,
+// per-width translation units (spmv_<pair>_<widths>.cu), which compile in
 // parallel.  The block width is a compile-time constant of each kernel
 // variant (the paper's fixed-loop-length code generation, Sec.
 // "Implementation"), padded to a power of two; a variant exists for every
@@ -32,7 +32,7 @@ namespace sp {
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS>
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
@@ -40,9 +40,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DM, MT, LS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DM, MT, LS>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI>,
                                                                       kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -75,7 +75,8 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     }
     b.nsm = sms;
     b.log2_tpr = lt;
-    k_spmmv<VT, XT, WP, VEC, DM, MT, LS><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
+    b.log2C = ilog2_exact(a.C);
+    k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
@@ -85,13 +86,25 @@ static int launch_spmv_wml(const SpmvArgs &a, bool vec, int max_blocks, cudaStre
     // dot set compiled in: none, <y,y> and <x,y>, or all three
     const uint32_t req = (a.flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY;
     if (req & 4)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS>(a, max_blocks, s);
+        return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS, 2>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS, 2>(a, max_blocks, s);
     if (req)
-        return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS>(a, max_blocks, s)
-                   : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS>(a, max_blocks, s);
-    return vec ? launch_spmv_variant<VT, XT, WP, true, 0, MT, LS>(a, max_blocks, s)
-               : launch_spmv_variant<VT, XT, WP, false, 0, MT, LS>(a, max_blocks, s);
+        return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS, 2>(a, max_blocks, s)
+                   : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS, 2>(a, max_blocks, s);
+    if constexpr (sizeof(XT) == 8) {
+        // float64 vectors: the plain product and the Chebyshev step get
+        // epilogues without runtime flags (no float64 work for flags that are off)
+        const uint32_t ef = a.flags & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT | SP_SPMV_SCALE | SP_SPMV_AXPBY |
+                                       SP_SPMV_CHAIN_AXPBY);
+        if (ef == 0)
+            return vec ? launch_spmv_variant<VT, XT, WP, true, 0, MT, LS, 0>(a, max_blocks, s)
+                       : launch_spmv_variant<VT, XT, WP, false, 0, MT, LS, 0>(a, max_blocks, s);
+        if (ef == (SP_SPMV_SCALE | SP_SPMV_AXPBY))
+            return vec ? launch_spmv_variant<VT, XT, WP, true, 0, MT, LS, 1>(a, max_blocks, s)
+                       : launch_spmv_variant<VT, XT, WP, false, 0, MT, LS, 1>(a, max_blocks, s);
+    }
+    return vec ? launch_spmv_variant<VT, XT, WP, true, 0, MT, LS, 2>(a, max_blocks, s)
+               : launch_spmv_variant<VT, XT, WP, false, 0, MT, LS, 2>(a, max_blocks, s);
 }
 
 // Lockstep row loop (row_product_ls) or per-lane loop: the lockstep form saves
@@ -115,24 +128,19 @@ static int launch_spmv_wm(const SpmvArgs &a, bool vec, int max_blocks, cudaStrea
     }
 }
 
+// Every kernel variant of one (value, vector) precision pair and one padded
+// width.  Instantiated by the spmv_<pair>_<widths>.cu units, a few widths
+// each, so that the variants compile in parallel; spmv_dispatch.cu picks the
+// width at run time (launch_spmv_typed).
 template <class VT, class XT, int WP>
-static int launch_spmv_w(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
+int launch_spmv_width(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     const bool mt = host_log2_tpr(a.C, WP / CPL) > 0;
     return mt ? launch_spmv_wm<VT, XT, WP, true>(a, vec, max_blocks, s)
               : launch_spmv_wm<VT, XT, WP, false>(a, vec, max_blocks, s);
 }
 
-template <class VT, class XT>
-int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
-    int w = a.w;
-    if (w <= 1) return launch_spmv_w<VT, XT, 1>(a, vec, max_blocks, s);
-    if (w <= 2) return launch_spmv_w<VT, XT, 2>(a, vec, max_blocks, s);
-    if (w <= 4) return launch_spmv_w<VT, XT, 4>(a, vec, max_blocks, s);
-    if (w <= 8) return launch_spmv_w<VT, XT, 8>(a, vec, max_blocks, s);
-    if (w <= 16) return launch_spmv_w<VT, XT, 16>(a, vec, max_blocks, s);
-    if (w <= 32) return launch_spmv_w<VT, XT, 32>(a, vec, max_blocks, s);
-    return SP_ERR_ARG;
-}
+#define SP_INSTANTIATE_WIDTH(VT, XT, WP) \
+    template int launch_spmv_width<VT, XT, WP>(const SpmvArgs &, bool, int, cudaStream_t);
 
 }  // namespace sp
