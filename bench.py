@@ -51,6 +51,8 @@ def algorithmic_bytes(nnz, nrows, ncols, nchunks, nslots, w, sv, sx, axpby, chai
     return int(b)
 
 
+METRIC = "SpMMV effective HBM GB/s (augmented SELL-32-256, f64, irregular N=2^21)"
+DATA = "synthetic (seeded irregular band matrix standing in for the paper's SuiteSparse inputs)"
 FP64_NOMINAL_TFLOPS = 1.25  # nominal dense float64 rate of a GB300 (context only)
 
 
@@ -67,7 +69,7 @@ def measured_fp64_rate():
             best = max(best, t)
     c = clk.summary()
     out = {"tflops": round(best, 4), "launch_ms": round(ms, 3), "clocks": c,
-           "method": "sp_device_fp64_rate: 2048 threads per SM x 8 independent fma chains x 16384 steps, "
+           "method": "sp_device_fp64_rate: 2048 threads per SM x 16 independent fma chains x 8192 steps, "
                      "best of 3 calls (each the best of 3 event-timed launches)"}
     if c and c.get("sm_mhz"):
         out["per_sm_per_cycle_fma"] = round(best * 1e12 / 2 / (c["sm_mhz"] * 1e6) / torch.cuda.get_device_properties(
@@ -286,6 +288,34 @@ def run_ours(args, rank, world):
         plan.close()
         h2d = X.nbytes + Y0.nbytes + Z0.nbytes
         d2h = Y0.nbytes + Z0.nbytes + 2 * 8
+
+        # per-call rates in the manner of the paper's spmvbench (Sec.
+        # "Heterogeneous execution"): P_max = the best of 100 calls, P_skip10 =
+        # the mean rate of all but the first ten; each call between its own events
+        calls = 100
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        per_ms = np.array([a.elapsed_time(b) for a, b in evs])
+        gf = 2.0 * A.nnz / (per_ms * 1e-3) / 1e9
+        gb = nbytes / (per_ms * 1e-3) / 1e9
+        spmvbench = {"calls": calls, "P_max_GFs": round(float(gf.max()), 2),
+                     "P_skip10_GFs": round(float(gf[10:].mean()), 2), "P_max_GBs": round(float(gb.max()), 1),
+                     "P_skip10_GBs": round(float(gb[10:].mean()), 1),
+                     "note": "GF/s = 2 nnz / call time, as the paper's spmvbench; GB/s = algorithmic bytes / call time"}
+
+        # value-only update (Sec. "Sparse matrix storage": a later construction
+        # with the same pattern only updates the values), values already on the
+        # device, against the product time
+        vdev = torch.from_numpy(A.val).to(dev)
+        mat.update_values(vdev, stream)
+        torch.cuda.synchronize()
+        upd_ms = _events_time(lambda: mat.update_values(vdev, stream), 10, stream)
+        del vdev
         for h in (hx, hy, hz):
             sellcs.sp_dense_destroy(h)
 
@@ -308,7 +338,7 @@ def run_ours(args, rank, world):
     roof = dict(alu if alu["frac"] > hbm["frac"] else hbm)
     roof["other"] = hbm if roof["bound"] == "alu" else alu
     result = {
-        "metric": "SpMMV effective HBM GB/s (augmented SELL-32-256, f64, irregular N=2^21)",
+        "metric": METRIC,
         "value": round(whole_job_rate(nbytes, ms_step, world) / 1e9, 2),
         "unit": "GB/s",
         "n_gpus": world,
@@ -319,9 +349,8 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded irregular band matrix standing in for the paper's SuiteSparse inputs)",
-        "config": dict(W, nnz=A.nnz, nstored=info["nstored"], bytes_per_call=nbytes,
-                       l2="inputs 0.96 GB > 129 MB L2, no flush", parallelism=f"replicas{world}"),
+        "data": DATA,
+        "config": workload_config(A, nbytes, world),
         "roofline": roof,
         "e2e": {"value": round(whole_job_rate(nbytes, e2e_ms, world) / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4),
@@ -329,7 +358,10 @@ def run_ours(args, rank, world):
                 "steps": e2e_steps},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
-        "setup": {"sell_build_s": round(setup_s, 4), "in_spmv_calls": round(setup_s / (ms_step * 1e-3), 1)},
+        "setup": {"nstored": info["nstored"], "sell_build_s": round(setup_s, 4), "in_spmv_calls": round(setup_s / (ms_step * 1e-3), 1),
+                  "update_values_device_ms": round(upd_ms, 4),
+                  "update_values_in_spmv_calls": round(upd_ms / ms_step, 2)},
+        "spmvbench": spmvbench,
     }
     return result, (A, X, Y0, Z0)
 
@@ -420,10 +452,15 @@ def _row_sample_csr(A, rows):
     return CSR(rows.size, A.ncols, rp, A.col[idx], A.val[idx])
 
 
-def secondary_anderson(peak):
+ANDERSON_PAIRS = [("f64", "f64"), ("f32", "f64"), ("bf16", "f64"), ("f32", "f32"), ("bf16", "f32")]
+
+
+def secondary_anderson(peak, pairs=None):
     """Anderson 128^3, width-16 Chebyshev step (alpha = 2/a, beta = -1) in each
-    precision pair: GB/s, speedup over f64, max error on 2048 sampled rows
-    against the f64 oracle (relative to max |y|)."""
+    precision pair (values, vectors): GB/s, speedup over f64, max error on 2048
+    sampled rows against the f64 oracle (relative to max |y|).  ``pairs``
+    restricts the run to some of the pairs (the speed-up is then relative to
+    the first pair run)."""
     import ctypes as ct
     import torch
     import oracle
@@ -437,7 +474,7 @@ def secondary_anderson(peak):
     yref = oracle.spmmv(sub, X, alpha=2 / a, beta=-1.0, y0=Y0[rows])[0]
     out = {}
     base = None
-    for vdt, xdt in [("f64", "f64"), ("f32", "f64"), ("bf16", "f64"), ("f32", "f32"), ("bf16", "f32")]:
+    for vdt, xdt in (pairs or ANDERSON_PAIRS):
         m = sellcs.SellMatrix(A, C=32, sigma=1, dtype=vdt)
         inf = m.info()
         tdt = torch.float64 if xdt == "f64" else torch.float32
@@ -538,7 +575,53 @@ def secondary_permuted(peak):
     return out
 
 
-def secondary_tsm(peak):
+def secondary_dist(peak):
+    """The row-partitioned product of the bench workload with P parts on this
+    one GPU (dist.LocalWorld: every part's halo pack, the halo copies and every
+    part's product, one after another on one stream), in the overlapped
+    two-pass form and the one-pass form, against the single product.  On one
+    GPU nothing overlaps: this measures what the split itself costs (the
+    two-pass form reads and writes y twice, as the paper notes for its
+    overlapped modes) and how large the halo is."""
+    import torch
+    from paper_1507_08101_gb300 import dist, sellcs
+    A, X, Y0, Z0 = make_workload()
+    W = WORKLOAD
+    nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, (A.nrows + 31) // 32, ((A.nrows + 31) // 32) * 32, 1, 8, 8,
+                           True, True, True)
+    kw = dict(alpha=W["alpha"], gamma=W["gamma"], beta=W["beta"], dot_xy=True, dot_yy=True, delta=W["delta"],
+              eta=W["eta"])
+    out = {}
+    m = sellcs.SellMatrix(A, C=W["C"], sigma=W["sigma"], dtype="f64")
+    x, y, z = (torch.from_numpy(v).cuda() for v in (X, Y0, Z0))
+    for _ in range(3):
+        sellcs.spmv(m, x, y, z=z, **kw)
+    torch.cuda.synchronize()
+    ms = _events_time(lambda: sellcs.spmv(m, x, y, z=z, **kw), 50, torch.cuda.current_stream())
+    out["single"] = {"us": round(ms * 1e3, 1), "GBs": round(nb / ms / 1e6, 1)}
+    m.close()
+    del x, y, z
+    for P in (2, 4):
+        for mode in ("overlap", "no_overlap"):
+            world = dist.LocalWorld(A, P, C=W["C"], sigma=W["sigma"], mode=mode)
+            xs = world.scatter(torch.from_numpy(X))
+            ys = [torch.from_numpy(Y0[world.bounds[r]:world.bounds[r + 1]]).cuda() for r in range(P)]
+            zs = [torch.from_numpy(Z0[world.bounds[r]:world.bounds[r + 1]]).cuda() for r in range(P)]
+            for _ in range(3):
+                world.spmv(xs, ys, zs, **kw)
+            torch.cuda.synchronize()
+            ms = _events_time(lambda: world.spmv(xs, ys, zs, **kw), 20, torch.cuda.current_stream())
+            halo = sum(p.info()["nhalo"] for p in world.plans)
+            rem = sum(p.info()["nnz_remote"] for p in world.plans)
+            out[f"P{P}_{mode}"] = {"us": round(ms * 1e3, 1), "GBs_of_single_bytes": round(nb / ms / 1e6, 1),
+                                   "halo_rows": int(halo), "remote_nnz_frac": round(rem / A.nnz, 4)}
+            for mm in world.mats:
+                mm.close()
+            del world, xs, ys, zs
+    return out
+
+
+def secondary_tsm(peak, dtypes=("f64", "f32")):
     """Tall and skinny kernels on n = 2^22 rows, m = k = 16: V^T W (plain and
     Kahan) and V X.  Bytes: V and W read once (tsmttsm); V read, W written
     (tsmm, beta = 0); flops 2 n m k."""
@@ -547,6 +630,8 @@ def secondary_tsm(peak):
     n, m, k = 1 << 22, 16, 16
     out = {"n": n, "m": m, "k": k}
     for dt, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        if dt not in dtypes:
+            continue
         g = torch.Generator(device="cuda").manual_seed(5)
         V = torch.rand(n, m, dtype=tdt, device="cuda", generator=g)
         W = torch.rand(n, k, dtype=tdt, device="cuda", generator=g)
@@ -614,9 +699,68 @@ def secondary_kpm(peak):
         torch.cuda.synchronize()
         unf = (time.perf_counter() - t0) / reps
         rel = float(np.max(np.abs(mu - mu_u.double().numpy()) / np.abs(mu[0])))
-        out[f"{vdt}_vals_{xdt}_vecs"] = {"fused_ms": round(fused * 1e3, 2), "per_product_us": round(fused / (nmom // 2) * 1e6, 1),
-                                         "unfused_ms": round(unf * 1e3, 2), "speedup_fused": round(unf / fused, 2),
-                                         "max_rel_diff_fused_vs_unfused": rel}
+        res = {"fused_ms": round(fused * 1e3, 2), "per_product_us": round(fused / (nmom // 2) * 1e6, 1),
+               "unfused_ms": round(unf * 1e3, 2), "speedup_fused": round(unf / fused, 2),
+               "max_rel_diff_fused_vs_unfused": rel}
+        # blocking (Sec. "Kernel fusion": blocking and fusion together): the
+        # same 16 starts run one vector at a time, fused and unfused
+        cols = [x[:, k:k + 1].contiguous() for k in range(x.shape[1])]
+        t0 = time.perf_counter()
+        for c in cols:
+            sellcs.kpm_moments(m, c, nmom, a, 0.0)
+        torch.cuda.synchronize()
+        f1 = time.perf_counter() - t0
+        x_all = x
+        t0 = time.perf_counter()
+        for c in cols:
+            x = c
+            unfused()
+        torch.cuda.synchronize()
+        u1 = time.perf_counter() - t0
+        x = x_all
+        res.update({"w1x16_fused_ms": round(f1 * 1e3, 2), "w1x16_unfused_ms": round(u1 * 1e3, 2),
+                    "speedup_blocking": round(f1 / fused, 2), "speedup_blocking_and_fusion": round(u1 / fused, 2)})
+        out[f"{vdt}_vals_{xdt}_vecs"] = res
+        m.close()
+    return out
+
+
+def secondary_layout(peak):
+    """Row-major (interleaved) against column-major block vectors (Sec. "Block
+    vectors"): the Anderson 128^3 Chebyshev step at width 16 (and 4) with x and
+    y in either layout, same algorithmic bytes."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    from workloads import generators as gen
+    A, X = gen.workload_anderson()
+    a = 1.01 * (6 + 8.25)
+    out = {}
+    for vdt, xdt in (("f64", "f64"), ("f32", "f32")):
+        tdt = torch.float64 if xdt == "f64" else torch.float32
+        m = sellcs.SellMatrix(A, C=32, sigma=1, dtype=vdt)
+        inf = m.info()
+        for w in (16, 4):
+            res = {}
+            for lay in ("row", "col"):
+                xr = torch.from_numpy(np.ascontiguousarray(X[:, :w])).to("cuda", tdt)
+                if lay == "row":
+                    x, y = xr, torch.zeros_like(xr)
+                    L = sellcs.SP_ROW_MAJOR
+                else:
+                    x = xr.t().contiguous().t()  # (N, w) with unit row stride
+                    y = torch.zeros_like(xr).t().contiguous().t()
+                    L = sellcs.SP_COL_MAJOR
+                for _ in range(3):
+                    sellcs.spmv(m, x, y, alpha=2 / a, beta=-1.0, layout=L)
+                torch.cuda.synchronize()
+                ms = _events_time(lambda: sellcs.spmv(m, x, y, alpha=2 / a, beta=-1.0, layout=L), 20,
+                                  torch.cuda.current_stream())
+                sv = 8 if vdt == "f64" else 4
+                nb = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * 32, w, sv, sv, True,
+                                       False, False)
+                res[lay] = {"us": round(ms * 1e3, 1), "GBs": round(nb / ms / 1e6, 1)}
+            res["row_over_col_speedup"] = round(res["col"]["us"] / res["row"]["us"], 3)
+            out[f"{vdt}_{xdt}_w{w}"] = res
         m.close()
     return out
 
@@ -699,53 +843,96 @@ def secondary_cg_batch(peak):
 # ------------------------------------------------------------------ CPU baseline (the oracle)
 
 
-def oracle_call(A, X, Y0, Z0):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_call(A, X, Y0, Z0, nthreads=1):
+    """One oracle product on the bench workload: the single-thread oracle, or
+    its row-parallel OpenMP form on ``nthreads`` host cores."""
     import oracle
     W = WORKLOAD
-    return oracle.spmmv(A, X, alpha=W["alpha"], gamma=W["gamma"], beta=W["beta"], y0=Y0, dot_xy=True, dot_yy=True,
-                        delta=W["delta"], eta=W["eta"], z0=Z0)
+    kw = dict(alpha=W["alpha"], gamma=W["gamma"], beta=W["beta"], y0=Y0, dot_xy=True, dot_yy=True,
+              delta=W["delta"], eta=W["eta"], z0=Z0)
+    if nthreads > 1:
+        r = oracle.spmmv_omp(A, X, nthreads=nthreads, **kw)
+        if r is not None:
+            return r
+    return oracle.spmmv(A, X, **kw)
+
+
+def _oracle_times(data, nthreads, reps, budget_s):
+    """Median seconds of up to ``reps`` oracle calls (at least 3, within budget_s)."""
+    A, X, Y0, Z0 = data
+    oracle_call(A, X, Y0, Z0, nthreads)
+    ts = []
+    t_start = time.time()
+    while len(ts) < reps and (len(ts) < 3 or time.time() - t_start < budget_s):
+        t0 = time.perf_counter()
+        oracle_call(A, X, Y0, Z0, nthreads)
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts)), len(ts)
+
+
+def workload_config(A, nbytes, world):
+    return dict(WORKLOAD, nnz=A.nnz, bytes_per_call=nbytes, l2="inputs 0.96 GB > 129 MB L2, no flush",
+                parallelism=f"replicas{world}")
 
 
 def cpu_baseline(data, budget_s=12.0):
+    """The oracle on the host: the row-parallel form over all cores (the
+    baseline value) and the single-thread form beside it, each the median of
+    10 full calls on the bench workload."""
     import oracle
-    A, X, Y0, Z0 = data
+    A = data[0]
     oracle.build()
     nch = (A.nrows + 31) // 32
     nbytes = algorithmic_bytes(A.nnz, A.nrows, A.ncols, nch, nch * 32, 1, 8, 8, True, True, True)
-    oracle_call(A, X, Y0, Z0)
-    t0 = time.time()
-    n = 0
-    while time.time() - t0 < budget_s and n < 50:
-        oracle_call(A, X, Y0, Z0)
-        n += 1
-    dt = (time.time() - t0) / n
-    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full calls of the float64 CSR oracle (Neumaier sums, single thread) on the same "
-                      f"workload, {dt:.3f} s each"}
+    cores = host_cores()
+    omp = oracle.build_omp() is not None and cores > 1
+    t1, n1 = _oracle_times(data, 1, 10, budget_s)
+    single = {"value": round(nbytes / t1 / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+              "sample": f"median of {n1} full calls of the float64 CSR oracle (Neumaier sums, single thread), "
+                        f"{t1:.3f} s each"}
+    if not omp:
+        return single
+    tn, nn = _oracle_times(data, cores, 10, budget_s)
+    return {"value": round(nbytes / tn / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"median of {nn} full calls of the float64 CSR oracle with its rows shared among {cores} "
+                      f"OpenMP threads (nproc = {cores}), {tn:.4f} s each",
+            "single_thread": single}
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the oracle, as it stands, on the host cores."""
+    """The reference arm: the oracle, as it stands (row-parallel over all host
+    cores when OpenMP is available), one full call per step."""
     import oracle
     oracle.build()
+    cores = host_cores()
+    nt = cores if oracle.build_omp() is not None else 1
     A, X, Y0, Z0 = make_workload()
     nch = (A.nrows + 31) // 32
     nbytes = algorithmic_bytes(A.nnz, A.nrows, A.ncols, nch, nch * 32, 1, 8, 8, True, True, True)
     for _ in range(args.warmup):
-        oracle_call(A, X, Y0, Z0)
+        oracle_call(A, X, Y0, Z0, nt)
     t0 = time.time()
     for _ in range(args.steps):
-        oracle_call(A, X, Y0, Z0)
+        oracle_call(A, X, Y0, Z0, nt)
     dt = (time.time() - t0) / args.steps
     v = round(nbytes / dt / 1e9, 3)
+    how = f"rows shared among {nt} OpenMP threads" if nt > 1 else "single thread"
     return {
         "impl": "reference",
-        "metric": "SpMMV effective HBM GB/s (augmented SELL-32-256, f64, irregular N=2^21)",
+        "metric": METRIC,
         "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD, nnz=A.nnz, bytes_per_call=nbytes),
-        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "one full oracle call per step (float64 CSR, Neumaier sums, single thread)"},
+        "dtype": "f64", "data": DATA, "config": workload_config(A, nbytes, world),
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": nt, "kind": "oracle",
+                         "sample": f"one full oracle call per step (float64 CSR, Neumaier sums, {how}; "
+                                   f"nproc = {cores})"},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -762,8 +949,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--only", choices=["laplace", "laplace256", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm",
-                                       "permuted", "tsm", "fp64_rate"],
+                                       "permuted", "tsm", "fp64_rate", "dist", "layout"],
                     help="run one secondary workload alone and print its JSON")
+    ap.add_argument("--pairs", default=None,
+                    help="with --only anderson_w16: comma-separated value:vector precision pairs, e.g. f32:f32; "
+                         "with --only tsm: the precisions, e.g. f32")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -779,9 +969,13 @@ def main():
         from paper_1507_08101_gb300 import build
         build.build()
         fns = {"laplace": secondary_laplace, "laplace256": lambda p: secondary_laplace(p, (256,)),
-               "fp64_rate": lambda p: measured_fp64_rate(), "anderson_w16": secondary_anderson,
+               "fp64_rate": lambda p: measured_fp64_rate(),
+               "anderson_w16": lambda p: secondary_anderson(
+                   p, [tuple(q.split(":")) for q in args.pairs.split(",")] if args.pairs else None),
+               "tsm": lambda p: secondary_tsm(p, tuple(args.pairs.split(",")) if args.pairs else ("f64", "f32")),
                "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
-               "permuted": secondary_permuted, "tsm": secondary_tsm}
+               "permuted": secondary_permuted, "dist": secondary_dist,
+               "layout": secondary_layout}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
         return
     if world > 1:

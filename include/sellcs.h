@@ -191,6 +191,35 @@ SP_API int sp_dense_data(const sp_dense *d, void **ptr, int64_t *nrows, int32_t 
 /* Frees the memory only if d owns it. */
 SP_API int sp_dense_destroy(sp_dense *d, void *stream);
 
+/*
+ * Scattered views and copies (Sec. "Dense matrices": a view may select a
+ * subset of a block's columns with gaps between them; a compact clone of such
+ * a view may be the better operand, and the storage layout can be changed
+ * while a block vector is copied).
+ *   sp_dense_view_scattered  view of the columns cols[0..ncols) (distinct,
+ *       each in [0, src->ncols); any order) of src (compact or scattered; the
+ *       view never owns memory).  SP_ERR_DIM for a column out of range,
+ *       SP_ERR_ARG for a repeated one.  Host only.
+ *   sp_dense_columns  writes the view's columns as columns of the block at its
+ *       base pointer (int32[ncols], may be NULL); returns 1 for a scattered
+ *       view, 0 for a compact one, <0 on error.  sp_dense_data returns that
+ *       base pointer for a scattered view.
+ *   sp_dense_clone    a new compact block (owned, nrows x ncols, `layout`)
+ *       holding a copy of src (any view).  Asynchronous after the allocation.
+ *   sp_dense_copy     dst = src for two views of equal shape and dtype, any
+ *       layouts and view kinds; SP_ERR_ARG if they share elements other than
+ *       as the identical view (then it is a no-op).  Asynchronous.
+ * sp_spmv accepts scattered x, y and z: it copies them into compact
+ * temporaries (stream-ordered allocations), runs the product, and copies y
+ * and z back; scattered x and y of one block must not share a column.  The
+ * other compute calls return SP_ERR_ARG for a scattered view (reason in
+ * sp_last_error_detail).
+ */
+SP_API int sp_dense_view_scattered(sp_dense **out, const sp_dense *src, int32_t ncols, const int32_t *cols);
+SP_API int sp_dense_columns(const sp_dense *d, int32_t *cols);
+SP_API int sp_dense_clone(sp_dense **out, const sp_dense *src, sp_layout layout, void *stream);
+SP_API int sp_dense_copy(sp_dense *dst, const sp_dense *src, void *stream);
+
 /* ------------------------------------------------------------------ augmented SpMMV */
 
 /* Augmentation flags (each enables one part; GHOST_SPMV_* in the paper). */
@@ -232,7 +261,10 @@ typedef struct {
  *   the epilogue runs in the vector precision).  Dot products are returned
  *   in double; they are accumulated in double for f64 vectors, and for f32
  *   vectors in float over short runs of rows (SP_DOT_RUN_F32), then double.
- *   SHIFT, VSHIFT, DOT_XY and DOT_XX need a square A.  SHIFT and VSHIFT are
+ *   SHIFT, VSHIFT, DOT_XY and DOT_XX need ncols(A) >= nrows(A); they use the
+ *   first nrows rows of x as the rows' own entries (I is the leading
+ *   nrows x nrows identity: a square A, or one process's rows with the columns
+ *   of its halo appended, see sp_dist_spmv).  SHIFT and VSHIFT are
  *   exclusive.  x must not overlap y or z, and z must not overlap y
  *   (SP_ERR_ARG).  The reductions are deterministic (fixed order).
  */
@@ -418,6 +450,115 @@ SP_API int sp_cg_solve(sp_cg *cg, const double *const *b, double *const *x, cons
                        sp_cg_stats *stats, double *rel_res, void *stream);
 SP_API int sp_cg_destroy(sp_cg *cg, void *stream);
 
+/* ------------------------------------------------------------------ row-partitioned product */
+
+/*
+ * The matrix distributed row-wise over processes (GHOST, Sec. "Data
+ * parallelism": the system matrix is split row-wise, the work of a process
+ * counted in rows or in nonzeros; Sec. "Heterogeneous execution": a share per
+ * process, e.g. its device's memory bandwidth, and the figure of the row-wise
+ * distribution: (1) weights, (2) one partial matrix per process, (3) the
+ * remote column indices compressed).  Only the host-side plan and two device
+ * calls live here; the exchange of the halo and the sum of the dot products
+ * over processes are the caller's (a collective library, or copies).
+ *
+ * sp_dist_partition: contiguous row blocks.  bounds (int64[nparts + 1],
+ * written) with bounds[0] = 0, bounds[nparts] = nrows, non-decreasing; part p
+ * owns rows [bounds[p], bounds[p+1]).  The work of rows [0, r) is r, or
+ * rowptr[r] when by_nnz (then rowptr is int64[nrows + 1] of the global CSR);
+ * each inner boundary is the row boundary nearest to the point where the work
+ * reaches the part's cumulative share (share: nparts finite weights >= 0, at
+ * least one positive; NULL = equal).  Host only.  SP_ERR_FORMAT for
+ * decreasing row pointers.
+ */
+SP_API int sp_dist_partition(int64_t nrows, const int64_t *rowptr, int nparts, const double *share, int by_nnz,
+                             int64_t *bounds);
+
+/*
+ * sp_dist_plan_create: the plan of process `rank` for its rows.
+ *   nglobal         global rows = global columns (square matrix)
+ *   nranks, bounds  the partition (int64[nranks + 1], as sp_dist_partition writes)
+ *   rowptr          int64[nloc + 1], rowptr[0] = 0: this process's rows only,
+ *                   nloc = bounds[rank+1] - bounds[rank]
+ *   gcol            int64[rowptr[nloc]] their GLOBAL column indices
+ * Column compression (step 3 of the figure): a column c owned by this
+ * process gets the local index c - bounds[rank]; the distinct remote columns,
+ * in ascending global order, get nloc, nloc + 1, ... ("the halo"), so the halo
+ * entries of one owner are contiguous and owners come in rank order.  Local
+ * indices are 32-bit (Sec. "Sparse matrix storage", local vs global indices):
+ * nloc + nhalo < 2^31 or SP_ERR_DIM.  Inputs are copied.  Host only.
+ * SP_ERR_FORMAT for bad row pointers or columns outside [0, nglobal).
+ *
+ * sp_dist_plan_info: nloc, nhalo, nonzeros in owned / remote columns, and the
+ *   rows this process sends (-1 before sp_dist_plan_set_sends).  Any output may
+ *   be NULL.
+ * sp_dist_plan_halo: halo_gidx (int64[nhalo]) the global row of each halo
+ *   entry; recv_counts (int64[nranks]) how many of them each rank owns (0 for
+ *   this rank).  Either may be NULL.
+ * sp_dist_plan_columns: col_ext (int32[nnz]) every entry's local column in
+ *   [0, nloc + nhalo), in the CSR order of the input: with the caller's
+ *   rowptr and values, the nloc x (nloc + nhalo) matrix of the "no overlap"
+ *   form (one product over x extended by its halo).
+ * sp_dist_plan_split: the same entries split into the local part (rowptr_loc
+ *   int64[nloc+1], col_loc int32, val_loc double: columns < nloc) and the
+ *   remote part (rowptr_rem, col_rem, val_rem: columns nloc..nloc+nhalo-1),
+ *   each row keeping its order; val is the double[nnz] of the input rows.
+ *   Arrays are caller-owned host memory sized by sp_dist_plan_info.
+ * sp_dist_plan_set_sends: what this process sends: send_counts (int64[nranks],
+ *   0 for itself) rows to each rank, send_gidx the global rows, rank after
+ *   rank, each list strictly ascending and owned by this process -- exactly
+ *   the halo_gidx of the receiving rank restricted to this process's rows (the
+ *   caller exchanges those lists once, e.g. with an all-to-all).  Host only;
+ *   SP_ERR_ARG with the reason in sp_last_error_detail for a bad list.
+ * sp_dist_plan_sends: the stored send counts (int64[nranks]) and local rows
+ *   (int32[nsend]); either may be NULL.  SP_ERR_ARG before set_sends.
+ * sp_dist_plan_destroy: frees the plan (and its device copy of the send list,
+ *   after synchronising that device).
+ */
+typedef struct sp_dist_plan sp_dist_plan;
+SP_API int sp_dist_plan_create(sp_dist_plan **out, int64_t nglobal, int nranks, const int64_t *bounds, int rank,
+                               const int64_t *rowptr, const int64_t *gcol);
+SP_API int sp_dist_plan_info(const sp_dist_plan *p, int64_t *nloc, int64_t *nhalo, int64_t *nnz_local,
+                             int64_t *nnz_remote, int64_t *nsend);
+SP_API int sp_dist_plan_halo(const sp_dist_plan *p, int64_t *halo_gidx, int64_t *recv_counts);
+SP_API int sp_dist_plan_columns(const sp_dist_plan *p, int32_t *col_ext);
+SP_API int sp_dist_plan_split(const sp_dist_plan *p, const double *val, int64_t *rowptr_loc, int32_t *col_loc,
+                              double *val_loc, int64_t *rowptr_rem, int32_t *col_rem, double *val_rem);
+SP_API int sp_dist_plan_set_sends(sp_dist_plan *p, const int64_t *send_counts, const int64_t *send_gidx);
+SP_API int sp_dist_plan_sends(const sp_dist_plan *p, int64_t *send_counts, int32_t *send_local);
+SP_API int sp_dist_plan_destroy(sp_dist_plan *p);
+
+/*
+ * sp_dist_pack: gathers the rows this process sends into send_buf (device,
+ * nsend x w row-major, contiguous, rank after rank as set_sends ordered them)
+ * from x (its first nloc rows; any layout; SP_F64 or SP_F32).  Asynchronous
+ * on `stream`, except the first call on a plan, which copies the send list to
+ * the device (cudaMalloc) and synchronises the stream.
+ *
+ * sp_dist_split_opts: the two passes of the overlapped product (host only):
+ * pass 1 = the request without dots, chain and DOT_HOST (y = alpha (A_loc x -
+ * gamma x) + beta y); pass 2 = y = alpha A_rem x + y (SCALE as requested,
+ * AXPBY with beta = 1) with the requested dots, chain and DOT_HOST.
+ *
+ * sp_dist_spmv: the overlapped product (task mode of Sec. "Resource
+ * management": the local part computed while the halo is in flight).
+ *   A_loc  nloc x nloc (the split's local part), A_rem nloc x (nloc + nhalo)
+ *   x      (nloc + nhalo) x w, row-major: rows 0..nloc-1 this process's x,
+ *          rows nloc.. the halo (received in halo_gidx order)
+ *   y, z   nloc x w; opts as sp_spmv
+ *   halo_ready  a cudaEvent_t recorded once the halo rows of x are written,
+ *          or NULL if they already are
+ * Pass 1 is enqueued on `stream` at once; the stream then waits for
+ * halo_ready and runs pass 2.  The dots are this process's partial sums:
+ * their sum over processes (3 w doubles) is the product's.  Shift and dots
+ * use x's first nloc rows.  y is read and written twice (the overlapped form
+ * stores the result twice, as the paper notes).
+ */
+SP_API int sp_dist_pack(sp_dist_plan *p, const sp_dense *x, void *send_buf, void *stream);
+SP_API int sp_dist_split_opts(const sp_spmv_opts *in, sp_spmv_opts *pass1, sp_spmv_opts *pass2);
+SP_API int sp_dist_spmv(sp_dense *y, const sp_mat *A_loc, const sp_mat *A_rem, const sp_dense *x,
+                        const sp_spmv_opts *opts, void *halo_ready, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation variant */
 
 /*
@@ -467,7 +608,7 @@ SP_API int sp_device_sm_count(int *count);
 /* Float64 fused multiply-add rate of the current device, measured (no
  * counterpart in the paper; the float64 products here are bound by that rate on
  * GB300, so their roofline needs the measured figure): every SM runs 2048
- * threads of 8 independent chains a <- fma(a, b, c) for 16384 steps; the best of
+ * threads of 16 independent chains a <- fma(a, b, c) for 8192 steps; the best of
  * three timed launches (CUDA events, after one warm-up launch) gives
  * *tflops = 2 x fused multiply-adds / time in TFLOP/s and *ms its duration
  * (ms may be NULL).  Synchronises the stream; allocates 8 bytes

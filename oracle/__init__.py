@@ -57,6 +57,70 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_LIBDIR, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False):
+    """The same C source with OpenMP (-fopenmp), for the all-cores timing
+    baseline (orc_spmmv_omp).  Returns the library path, or None when the
+    compiler cannot build it."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".{os.getpid()}.tmp"
+        try:
+            subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c99", "-fopenmp",
+                                   "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except (OSError, subprocess.CalledProcessError):
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    if _lib_omp is None:
+        if build_omp() is None:
+            return None
+        L = ct.CDLL(_LIB_OMP)
+        P, I64, I, D = ct.c_void_p, ct.c_int64, ct.c_int, ct.c_double
+        L.orc_spmmv_omp.restype = None
+        L.orc_spmmv_omp.argtypes = [I64, P, P, P, I, P, I64, P, I64, P, I64,
+                                    I, D, I, P, I, D, I, I, I, P, I, D, D, P, I64, I]
+        _lib_omp = L
+    return _lib_omp
+
+
+def spmmv_omp(A, x, *, nthreads, alpha=None, gamma=None, beta=None, y0=None, dot_yy=False, dot_xy=False,
+              dot_xx=False, delta=None, eta=None, z0=None):
+    """spmmv with the rows shared among ``nthreads`` OpenMP threads (timing
+    baseline only; see orc_spmmv_omp).  Same return values as spmmv; None if
+    OpenMP is not available."""
+    lib = _load_omp()
+    if lib is None:
+        return None
+    x = np.asarray(x, np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    x = _c(x, np.float64)
+    N, w = A.nrows, x.shape[1]
+    y = np.empty((N, w), np.float64)
+    g = np.zeros(w) if gamma is None else np.broadcast_to(np.asarray(gamma, np.float64), (w,)).copy()
+    do_axpby = beta is not None
+    y0c = _c(y0, np.float64).reshape(N, w) if do_axpby else np.zeros((1, 1))
+    do_chain = z0 is not None
+    z = _c(z0, np.float64).reshape(N, w).copy() if do_chain else np.zeros((1, 1))
+    dot = np.full(3 * w, np.nan)
+    lib.orc_spmmv_omp(N, _p(_c(A.rowptr, np.int64)), _p(_c(A.col, np.int32)), _p(_c(A.val, np.float64)), w,
+                      _p(x), w, _p(y), w, _p(y0c), w,
+                      int(alpha is not None), float(alpha if alpha is not None else 1.0),
+                      int(gamma is not None), _p(g), int(do_axpby), float(beta if do_axpby else 0.0),
+                      int(dot_yy), int(dot_xy), int(dot_xx), _p(dot),
+                      int(do_chain), float(delta if do_chain else 0.0), float(eta if do_chain else 0.0),
+                      _p(z), w, int(nthreads))
+    return y, dot, (z if do_chain else None)
+
+
 def _load():
     global _lib
     if _lib is None:

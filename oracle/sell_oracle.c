@@ -26,12 +26,17 @@
  *  - a padded entry stores value 0 and the column of the last real entry of
  *    its row (column 0 for an empty row or a padding row); a padding row (the
  *    tail of the last chunk) has length 0 and permutation entry -1;
- *  - the dot products and z use the NEW y.
+ *  - the dot products and z use the NEW y;
+ *  - with more columns than rows, the shift and the x-dots take x's first
+ *    N rows (I is the leading N x N identity).
  *
  * Sums (row sums and dot products) use Neumaier's compensated summation so the
  * oracle's own rounding error is far below that of the kernels it checks.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -174,7 +179,10 @@ void orc_spmmv(int64_t N, int64_t ncols, const int64_t *rowptr, const int32_t *c
             nsum t = {0.0, 0.0};
             for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) nsum_add(&t, val[p] * x[col[p] * ldx + k]);
             double r = nsum_get(&t);
-            double xi = x[i * ldx + k]; /* square matrix: row i of x is column i of A */
+            /* row i of x is column i of A: the identity of the shift is the
+             * leading N x N block (ncols >= N: a square A, or one process's
+             * rows with the columns of its halo appended) */
+            double xi = x[i * ldx + k];
             if (do_shift) r = r - gamma[k] * xi;
             r = a * r;
             if (do_axpby) r = r + beta * y0[i * ldy0 + k];
@@ -193,6 +201,62 @@ void orc_spmmv(int64_t N, int64_t ncols, const int64_t *rowptr, const int32_t *c
     free(dyy);
     free(dxy);
     free(dxx);
+}
+
+/* The same product with the rows shared among OpenMP threads (a timing
+ * baseline over all host cores; the tests pin orc_spmmv, and check that this
+ * one gives the same y and z and dots equal to rounding).  Each thread keeps
+ * its own compensated dot sums over a contiguous block of rows; the blocks'
+ * sums are added in block order.  Without -fopenmp it runs on one thread. */
+void orc_spmmv_omp(int64_t N, const int64_t *rowptr, const int32_t *col, const double *val, int w,
+                   const double *x, int64_t ldx, double *y, int64_t ldy, const double *y0, int64_t ldy0,
+                   int do_scale, double alpha, int do_shift, const double *gamma, int do_axpby, double beta,
+                   int dot_yy, int dot_xy, int dot_xx, double *dot, int do_chain, double delta, double eta,
+                   double *z, int64_t ldz, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    nsum *part = (nsum *)calloc((size_t)nthreads * 3 * (size_t)w, sizeof(nsum));
+    const double a = do_scale ? alpha : 1.0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int tid = 0, nt = 1;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        const int64_t i0 = N * tid / nt, i1 = N * (tid + 1) / nt;
+        nsum *dyy = part + (size_t)tid * 3 * w, *dxy = dyy + w, *dxx = dxy + w;
+        for (int64_t i = i0; i < i1; ++i) {
+            for (int k = 0; k < w; ++k) {
+                nsum t = {0.0, 0.0};
+                for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) nsum_add(&t, val[p] * x[col[p] * ldx + k]);
+                double r = nsum_get(&t);
+                double xi = x[i * ldx + k];
+                if (do_shift) r = r - gamma[k] * xi;
+                r = a * r;
+                if (do_axpby) r = r + beta * y0[i * ldy0 + k];
+                y[i * ldy + k] = r;
+                if (dot_yy) nsum_add(&dyy[k], r * r);
+                if (dot_xy) nsum_add(&dxy[k], xi * r);
+                if (dot_xx) nsum_add(&dxx[k], xi * xi);
+                if (do_chain) z[i * ldz + k] = delta * z[i * ldz + k] + eta * r;
+            }
+        }
+    }
+    for (int k = 0; k < w; ++k) {
+        nsum s[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        for (int t = 0; t < nthreads; ++t)
+            for (int q = 0; q < 3; ++q) {
+                const nsum *v = part + (size_t)t * 3 * w + (size_t)q * w + k;
+                nsum_add(&s[q], v->s);
+                nsum_add(&s[q], v->c);
+            }
+        if (dot_yy) dot[k] = nsum_get(&s[0]);
+        if (dot_xy) dot[w + k] = nsum_get(&s[1]);
+        if (dot_xx) dot[2 * w + k] = nsum_get(&s[2]);
+    }
+    free(part);
 }
 
 /* |A| |x| + |alpha gamma| |x| + |beta| |y0| per entry: the scale against

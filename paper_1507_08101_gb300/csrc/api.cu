@@ -12,6 +12,7 @@
 namespace sp {
 template <class VT, class XT>
 int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
+int spmv_scattered(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts &o, void *stream);
 }
 
 static thread_local char g_detail[512] = "";
@@ -505,8 +506,14 @@ int sp_dense_view_cols(sp_dense **out, const sp_dense *src, int32_t col0, int32_
     *d = *src;
     d->owner.reset();
     d->ncols = ncols;
-    size_t es = dtype_size(src->dtype);
-    d->ptr = (char *)src->ptr + (size_t)col0 * (src->layout == SP_ROW_MAJOR ? 1 : src->ld) * es;
+    if (src->cols) {
+        // a run of a scattered view's columns is scattered too
+        d->cols = std::make_shared<const std::vector<int32_t>>(src->cols->begin() + col0,
+                                                               src->cols->begin() + col0 + ncols);
+    } else {
+        size_t es = dtype_size(src->dtype);
+        d->ptr = (char *)src->ptr + (size_t)col0 * (src->layout == SP_ROW_MAJOR ? 1 : src->ld) * es;
+    }
     *out = d;
     return SP_OK;
 }
@@ -536,6 +543,9 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
     static const sp_spmv_opts defaults = SP_SPMV_OPTS_INIT;
     if (!y || !A || !x) return SP_ERR_ARG;
     const sp_spmv_opts &o = opts ? *opts : defaults;
+    // scattered views: the product runs on compact clones, copied back
+    if (dense_scattered(x) || dense_scattered(y) || ((o.flags & SP_SPMV_CHAIN_AXPBY) && dense_scattered(o.z)))
+        return spmv_scattered(y, A, x, o, stream);
     const uint32_t known = SP_SPMV_SCALE | SP_SPMV_SHIFT | SP_SPMV_VSHIFT | SP_SPMV_AXPBY | SP_SPMV_DOT_ANY |
                            SP_SPMV_CHAIN_AXPBY | SP_SPMV_DOT_HOST;
     uint32_t f = o.flags;
@@ -550,7 +560,10 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
     if ((f & SP_SPMV_SHIFT) && (f & SP_SPMV_VSHIFT)) return SP_ERR_ARG;
     if (shift && !o.gamma) return SP_ERR_ARG;
     if ((f & SP_SPMV_VSHIFT) && w > SP_MAX_VSHIFT) return SP_ERR_ARG;
-    if ((shift || (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX))) && P.nrows != P.ncols) return SP_ERR_DIM;
+    // the identity of the shift (and x_i in the dots) is the leading nrows x nrows
+    // block: x's first nrows rows (a square A, or a process's rows [A_loc | A_rem]
+    // over x extended by its halo)
+    if ((shift || (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX))) && P.ncols < P.nrows) return SP_ERR_DIM;
     if ((f & SP_SPMV_DOT_ANY) && !o.dot) return SP_ERR_ARG;
     bool chain = f & SP_SPMV_CHAIN_AXPBY;
     if (chain) {
@@ -616,6 +629,7 @@ int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *
                     void *stream) {
     if (A && A->pat->permuted_space) return SP_ERR_ARG;  // the adjoint works in the user's order
     if (!A || !g) return SP_ERR_ARG;
+    if (dense_scattered(dx) || dense_scattered(x) || dense_scattered(g)) return sp::scattered_refused("sp_spmv_adjoint");
     const Pattern &P = *A->pat;
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nrows != P.nrows) return SP_ERR_DIM;
@@ -661,6 +675,7 @@ __global__ void k_permute_rows(const int32_t *__restrict__ perm, int64_t nrows, 
 
 extern "C" int sp_mat_permute(const sp_mat *A, sp_dense *out, const sp_dense *in, int to_sell, void *stream) {
     if (!A || !out || !in) return SP_ERR_ARG;
+    if (sp::dense_scattered(out) || sp::dense_scattered(in)) return sp::scattered_refused("sp_mat_permute");
     const sp::Pattern &P = *A->pat;
     if (in->nrows != P.nrows || out->nrows != P.nrows || in->ncols != out->ncols) return SP_ERR_DIM;
     if (in->dtype != out->dtype || (in->dtype != SP_F64 && in->dtype != SP_F32)) return SP_ERR_DTYPE;

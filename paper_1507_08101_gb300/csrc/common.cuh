@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <memory>
+#include <vector>
 
 #include "../../include/sellcs.h"
 
@@ -124,11 +125,22 @@ struct sp_dense {
     sp_dtype dtype = SP_F64;
     sp_layout layout = SP_ROW_MAJOR;
     sp::DevBufPtr owner;  // set when the library allocated the memory
+    // scattered view: column c of the view is column cols[c] of the block at
+    // ptr (null for a compact block or view)
+    std::shared_ptr<const std::vector<int32_t>> cols;
 };
 
 namespace sp {
 
 inline size_t dtype_size(sp_dtype t) { return t == SP_F64 ? 8 : (t == SP_F32 ? 4 : 2); }
+
+// Scattered views are accepted by sp_spmv (through compact clones) and by the
+// dense copy calls; the other entry points refuse them.
+inline bool dense_scattered(const sp_dense *d) { return d && d->cols; }
+inline int scattered_refused(const char *who) {
+    sp_internal_set_detail(who, "a scattered view is not accepted here: make a compact clone (sp_dense_clone)");
+    return SP_ERR_ARG;
+}
 
 inline int ilog2_exact(int64_t v) {
     int l = 0;

@@ -43,6 +43,7 @@ __global__ void k_kpm_assemble(const double *__restrict__ d, int w, int nmom, do
 }  // namespace sp
 
 int sp_kpm_moments(const sp_mat *A, const sp_dense *x, int32_t nmom, double a, double b, double *mu, void *stream) {
+    if (sp::dense_scattered(x)) return sp::scattered_refused("sp_kpm_moments");
     if (!A || !x || !mu || nmom < 1) return SP_ERR_ARG;
     if (!(a != 0.0) || !std::isfinite(a) || !std::isfinite(b)) return SP_ERR_ARG;
     const sp::Pattern &P = *A->pat;

@@ -3,7 +3,7 @@
 // their roofline needs the pipe's rate on the machine at hand rather than a
 // nominal figure.
 //
-// k_dfma_chains: every thread runs kChains independent chains of fused
+// k_dfma_chains: every thread runs kChains (16) independent chains of fused
 // multiply-adds a <- a * b + c (kChains in flight hide the pipe latency), for
 // `iters` steps; the grid holds every SM with 2048 threads.  b slightly below 1
 // and c small keep the values bounded and normal.  One thread whose result can
@@ -12,16 +12,20 @@
 
 namespace sp {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 constexpr int kPeakThreads = 256;
 
 __global__ void __launch_bounds__(kPeakThreads) k_dfma_chains(int iters, double b, double c, double *sink) {
     double a[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
-    for (int i = 0; i < iters; ++i) {
+    // four steps per loop trip, so the loop's own integer work is a small
+    // share of the issue slots
+    for (int i = 0; i < iters; i += 4) {
 #pragma unroll
-        for (int k = 0; k < kChains; ++k) a[k] = __fma_rn(a[k], b, c);
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = __fma_rn(a[k], b, c);
     }
     double s = 0.0;
 #pragma unroll
@@ -37,7 +41,7 @@ extern "C" int sp_device_fp64_rate(double *tflops, double *ms, void *stream) {
     int sms = 1;
     SP_TRY(sp::device_sm_count(&sms));
     const int blocks = sms * (2048 / sp::kPeakThreads);
-    const int iters = 1 << 14;
+    const int iters = 1 << 13;
     sp::Tmp sink(s);
     SP_TRY(sink.alloc(sizeof(double)));
     cudaEvent_t e0, e1;

@@ -330,6 +330,62 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
     }
 }
 
+// The last (fewer than U) entries of a row loop.  `steps` (1..U) is how
+// many multiply-adds the warp has to issue: in the lockstep loop the entries
+// left in the longest row of the chunk (the same for every lane of it), in
+// the per-lane loop U.  Slot k of the unrolled
+// sequence holds entry k - (U - steps), so the loads and gathers all go out
+// at once, and a jump into the sequence (fall-through switch) issues exactly
+// `steps` multiply-adds, in entry order: a multiply-add under a false
+// predicate would cost as much as a real one on GB300's float64 pipe (a
+// predicated-off lane still occupies its slot of the warp instruction).
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT>
+__device__ __forceinline__ void tail_steps(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
+                                           int rest, int steps, const XT *__restrict__ xk, int64_t xrs,
+                                           int64_t xcs, int nvalid, AT (&acc)[CPL], int &bad) {
+    static_assert(U >= 1 && U <= 8, "tail unroll");
+    const int sh = U - steps;
+    int32_t cc[U];
+    VT vv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const int e = k - sh;
+        const bool ok = e >= 0 && e < rest;
+        cc[k] = ok ? ld_stream(cp + (int64_t)e * C) : 0;
+        vv[k] = ok ? ld_stream(vp + (int64_t)e * C) : VT(0);
+    }
+    if (nvalid <= 0) return;
+    XT xv[U][CPL];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const int e = k - sh;
+        if (e >= 0 && e < rest) {
+            load_cols<XT, CPL, VEC>(xk + (int64_t)cc[k] * xrs, xcs, nvalid, xv[k]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) xv[k][c] = XT(0);
+        }
+    }
+    auto step = [&](int k) {
+        if (k - sh < rest) {
+            const AT v = val_to_acc<AT, VT>(vv[k]);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[k][c], bad), acc[c]);
+        }
+    };
+    switch (sh) {
+        case 0: if (U > 0) step(0); [[fallthrough]];
+        case 1: if (U > 1) step(1); [[fallthrough]];
+        case 2: if (U > 2) step(2); [[fallthrough]];
+        case 3: if (U > 3) step(3); [[fallthrough]];
+        case 4: if (U > 4) step(4); [[fallthrough]];
+        case 5: if (U > 5) step(5); [[fallthrough]];
+        case 6: if (U > 6) step(6); [[fallthrough]];
+        case 7: if (U > 7) step(7); [[fallthrough]];
+        default: break;
+    }
+}
+
 // Lockstep form of row_product: every lane of a chunk steps through the
 // chunk's length clen (the same for all of them), and the entries past a lane's
 // own row length are predicated off.  The warp then issues one step per column
@@ -343,6 +399,7 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
 #ifndef SP_LOCKSTEP
 #define SP_LOCKSTEP 1
 #endif
+
 // Longest run of row iterations over which a lane of a float32-vector product
 // accumulates its dot products in float (SP_DOT_RUN_F32, defined in the header).
 static_assert(SP_DOT_RUN_F32 >= 1, "dot run length");
@@ -381,28 +438,7 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
             }
         }
     }
-    const int rest = len - j;
-    if (clen > j) {
-        int32_t cc[U];
-        VT vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
-            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : VT(0);
-        }
-        if (nvalid > 0) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (u < rest) {
-                    XT xv[CPL];
-                    load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
-                    AT v = val_to_acc<AT, VT>(vv[u]);
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
-                }
-            }
-        }
-    }
+    if (clen > j) tail_steps<VT, XT, AT, CPL, VEC, U, EXACT>(vp, cp, C, len - j, clen - j, xk, xrs, xcs, nvalid, acc, bad);
 }
 
 // Row sums t[c] = sum_j val(s,j) * x[col(s,j), k0 + c] for the row in one slot.
@@ -436,28 +472,10 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
             }
         }
     }
+    // lanes run rows of their own lengths here, so no count shorter than U
+    // bounds every lane's tail: all U steps, each under its lane's predicate
     const int rest = len - j;
-    if (rest > 0) {
-        int32_t cc[U];
-        VT vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            cc[u] = u < rest ? ld_stream(cp + (int64_t)u * C) : 0;
-            vv[u] = u < rest ? ld_stream(vp + (int64_t)u * C) : VT(0);
-        }
-        if (nvalid > 0) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (u < rest) {
-                    XT xv[CPL];
-                    load_cols<XT, CPL, VEC>(xk + (int64_t)cc[u] * xrs, xcs, nvalid, xv);
-                    AT v = val_to_acc<AT, VT>(vv[u]);
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) acc[c] = fma(v, x_to_acc<AT, XT, EXACT>(xv[c], bad), acc[c]);
-                }
-            }
-        }
-    }
+    if (rest > 0) tail_steps<VT, XT, AT, CPL, VEC, U, EXACT>(vp, cp, C, rest, U, xk, xrs, xcs, nvalid, acc, bad);
 }
 
 // Per-warp float64 sums of the dot products in shared memory: the warp's

@@ -40,6 +40,10 @@ constexpr int kTsmStages = 2;           // tiles per block in shared memory (rin
 constexpr int kTsmTileBytes = 24576;    // bytes of V (and W) per staged tile
 constexpr int kTsmMaxBlocksPerSm = 4;
 constexpr size_t kTsmSmemMax = 48 * 1024;  // dynamic shared memory without an opt-in attribute
+// 1: tiles of dense blocks move by one bulk copy each (cp.async.bulk + mbarrier)
+#ifndef SP_TSM_BULK
+#define SP_TSM_BULK 1
+#endif
 
 // ------------------------------------------------------------------ cp.async staging
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -102,6 +106,47 @@ __device__ __forceinline__ void stage_contig(T *dst, const T *__restrict__ src, 
     for (int e = threadIdx.x; e < pieces; e += kTsmThreads) cp_async<16>(dst + e * E, src + e * E);
 }
 
+// ------------------------------------------------------------------ bulk-copy staging
+// One thread copies a whole tile of rows that are contiguous in global memory
+// with one cp.async.bulk (the copy engine moves it; no per-thread copy
+// instructions), completing on the stage's mbarrier with the tile's byte
+// count.  Waits are bounded: a wait that runs out records the failure in the
+// call's status word (the final kernel then writes NaN into X) and the block
+// stops working on its tiles.
+constexpr int kTsmBulkStages = 4;
+constexpr int kTsmBulkTileBytes = 12288;
+constexpr unsigned kTsmWaitTries = 1u << 22;  // try_wait rounds (each suspends for a while) before giving up
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// true when the phase with this parity completed within the bound
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+    for (unsigned i = 0; i < kTsmWaitTries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // N consecutive elements from 16-byte-aligned (N * sizeof(T) >= 16) or
 // N * sizeof(T)-aligned shared memory.
 template <class T, int N>
@@ -140,8 +185,8 @@ __device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
 }
 
 // Rows per staged tile for `row_bytes` bytes of shared memory per row.
-inline int tile_rows(int row_bytes) {
-    int tr = kTsmTileBytes / row_bytes;
+inline int tile_rows(int row_bytes, int tile_bytes = kTsmTileBytes) {
+    int tr = tile_bytes / row_bytes;
     tr = std::max(32, std::min(1024, tr / 32 * 32));
     return tr;
 }
@@ -169,59 +214,46 @@ __device__ __forceinline__ void outer_acc(T (&acc)[RA * RB], T (&cmp)[RA * RB], 
 }
 
 // part[(a * k + b) * nb + block] = (s, c) of the block's sum for output (a, b)
-template <class T, bool KAHAN, int RA, int RB, int LA, int LB>
+template <class T, bool KAHAN, int RA, int RB, int LA, int LB, bool BULK>
 __global__ void __launch_bounds__(kTsmThreads, RA * RB > 16 ? 1 : (KAHAN ? 2 : 4)) k_tsmttsm_tile(const T *__restrict__ V, int64_t ldv,
                                                               const T *__restrict__ W, int64_t ldw, int64_t n, int m,
                                                               int k, int tr, int64_t tiles_per_block, int vec,
-                                                              Comp *__restrict__ part) {
+                                                              Comp *__restrict__ part, unsigned *status) {
     constexpr int L = LA * LB, G = kTsmThreads / L, MPs = LA * RA, KPs = LB * RB, RR = RA * RB;
+    constexpr int S = BULK ? kTsmBulkStages : kTsmStages;
     extern __shared__ __align__(16) unsigned char tsm_smem[];
     T *const st = reinterpret_cast<T *>(tsm_smem);
     const int t = threadIdx.x, l = t % L, g = t / L, ia = l / LB, ib = l % LB;
     const int stage_elems = tr * (MPs + KPs);
-    // padding columns (never written by the copies) hold zeros
-    for (int e = t; e < kTsmStages * stage_elems; e += kTsmThreads) {
-        const int o = e % stage_elems;
-        const bool pad = o < tr * MPs ? (o % MPs) >= m : ((o - tr * MPs) % KPs) >= k;
-        if (pad) st[e] = T(0);
+    // BULK: the rows of V and W are contiguous and fill the tile's rows (no
+    // padding columns); the stages' mbarriers follow the tiles
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(st + S * stage_elems);
+    if constexpr (!BULK) {
+        // padding columns (never written by the copies) hold zeros
+        for (int e = t; e < kTsmStages * stage_elems; e += kTsmThreads) {
+            const int o = e % stage_elems;
+            const bool pad = o < tr * MPs ? (o % MPs) >= m : ((o - tr * MPs) % KPs) >= k;
+            if (pad) st[e] = T(0);
+        }
+    } else {
+        if (t == 0) {
+            for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
+            mbar_fence_init();
+        }
     }
+    __shared__ int failed;  // a copy wait ran out (bulk staging)
+    if (t == 0) failed = 0;
+    __syncthreads();
     T acc[RR], cmp[RR];
 #pragma unroll
     for (int x = 0; x < RR; ++x) acc[x] = cmp[x] = T(0);
     const int64_t ntiles = (n + tr - 1) / tr;
     const int64_t tile0 = (int64_t)blockIdx.x * tiles_per_block;
     const int64_t tile1 = ntiles < tile0 + tiles_per_block ? ntiles : tile0 + tiles_per_block;
-    // rows of V (W) that are contiguous in memory and fill the tile's rows exactly
-    const bool dense_v = (vec & 1) && ldv == m && MPs == m, dense_w = (vec & 2) && ldw == k && KPs == k;
-    auto stage = [&](int64_t tile, int s) {
-        T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
-        const int64_t r0 = tile * tr;
-        const int rows = (int)(n - r0 < tr ? n - r0 : tr);
-        if (dense_v)
-            stage_contig(sv, V + r0 * ldv, rows * (MPs * (int)sizeof(T) / 16));
-        else
-            stage_rows(sv, MPs, V, ldv, r0, rows, m, vec & 1);
-        if (dense_w)
-            stage_contig(sw, W + r0 * ldw, rows * (KPs * (int)sizeof(T) / 16));
-        else
-            stage_rows(sw, KPs, W, ldw, r0, rows, k, (vec & 2) != 0);
-    };
-    // one commit group per tile (empty past the end), so that waiting for all
-    // but the newest kTsmStages - 1 groups leaves this tile complete
-#pragma unroll
-    for (int i = 0; i < kTsmStages - 1; ++i) {
-        if (tile0 + i < tile1) stage(tile0 + i, i);
-        cp_async_commit();
-    }
-    for (int64_t tile = tile0; tile < tile1; ++tile) {
-        const int it = (int)(tile - tile0), s = it % kTsmStages;
-        if (tile + kTsmStages - 1 < tile1) stage(tile + kTsmStages - 1, (it + kTsmStages - 1) % kTsmStages);
-        cp_async_commit();
-        cp_async_wait<kTsmStages - 1>();
-        __syncthreads();
-        const T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
+    // the compute of one staged tile (rows g, g + G, ...: two per step)
+    auto work = [&](int si, int64_t tile) {
+        const T *sv = st + si * stage_elems, *sw = sv + tr * MPs;
         const int rows = (int)(n - tile * tr < tr ? n - tile * tr : tr);
-        // rows g, g + G, ...: two per step
         const T *pv = sv + g * MPs + ia * RA, *pw = sw + g * KPs + ib * RB;
         int r = g;
         for (; r + G < rows; r += 2 * G, pv += 2 * G * MPs, pw += 2 * G * KPs) {
@@ -239,7 +271,78 @@ __global__ void __launch_bounds__(kTsmThreads, RA * RB > 16 ? 1 : (KAHAN ? 2 : 4
             ld_vec<T, RB>(pw, wb);
             outer_acc<T, KAHAN, RA, RB>(acc, cmp, va, wb);
         }
-        __syncthreads();
+    };
+    if constexpr (BULK) {
+        // thread 0 keeps up to S tiles in flight; tile i lands in stage i mod S,
+        // whose mbarrier completes its (i / S)-th phase
+        auto issue = [&](int64_t tile, int si) {
+            T *sv = st + si * stage_elems, *sw = sv + tr * MPs;
+            const int64_t r0 = tile * tr;
+            const int rows = (int)(n - r0 < tr ? n - r0 : tr);
+            const unsigned bv = (unsigned)(rows * m * (int)sizeof(T)), bw = (unsigned)(rows * k * (int)sizeof(T));
+            mbar_expect_tx(&bars[si], bv + bw);
+            bulk_to_smem(sv, V + r0 * ldv, bv, &bars[si]);
+            bulk_to_smem(sw, W + r0 * ldw, bw, &bars[si]);
+        };
+        if (t == 0)
+            for (int i = 0; i < S && tile0 + i < tile1; ++i) issue(tile0 + i, i);
+        int64_t tile = tile0;
+        for (; tile < tile1; ++tile) {
+            const int it = (int)(tile - tile0), si = it % S;
+            if (!mbar_wait_bounded(&bars[si], (unsigned)(it / S) & 1u)) atomicOr(&failed, 1);
+            __syncthreads();
+            if (failed) break;
+            work(si, tile);
+            __syncthreads();  // every thread is done with stage si
+            if (t == 0 && tile + S < tile1) {
+                fence_proxy_async_smem();
+                issue(tile + S, si);
+            }
+        }
+        if (failed) {
+            // leave no copy running into this block's shared memory: wait
+            // (bounded) for every tile issued after the one that failed
+            if (t == 0) {
+                for (int64_t u = tile; u < tile1 && u < tile + S; ++u) {
+                    const int iu = (int)(u - tile0);
+                    mbar_wait_bounded(&bars[iu % S], (unsigned)(iu / S) & 1u);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // rows of V (W) that are contiguous in memory and fill the tile's rows exactly
+    const bool dense_v = (vec & 1) && ldv == m && MPs == m, dense_w = (vec & 2) && ldw == k && KPs == k;
+    auto stage = [&](int64_t tile, int s) {
+        T *sv = st + s * stage_elems, *sw = sv + tr * MPs;
+        const int64_t r0 = tile * tr;
+        const int rows = (int)(n - r0 < tr ? n - r0 : tr);
+        if (dense_v)
+            stage_contig(sv, V + r0 * ldv, rows * (MPs * (int)sizeof(T) / 16));
+        else
+            stage_rows(sv, MPs, V, ldv, r0, rows, m, vec & 1);
+        if (dense_w)
+            stage_contig(sw, W + r0 * ldw, rows * (KPs * (int)sizeof(T) / 16));
+        else
+            stage_rows(sw, KPs, W, ldw, r0, rows, k, (vec & 2) != 0);
+    };
+    if constexpr (!BULK) {
+        // one commit group per tile (empty past the end), so that waiting for all
+        // but the newest kTsmStages - 1 groups leaves this tile complete
+#pragma unroll
+        for (int i = 0; i < kTsmStages - 1; ++i) {
+            if (tile0 + i < tile1) stage(tile0 + i, i);
+            cp_async_commit();
+        }
+        for (int64_t tile = tile0; tile < tile1; ++tile) {
+            const int it = (int)(tile - tile0), si = it % kTsmStages;
+            if (tile + kTsmStages - 1 < tile1) stage(tile + kTsmStages - 1, (it + kTsmStages - 1) % kTsmStages);
+            cp_async_commit();
+            cp_async_wait<kTsmStages - 1>();
+            __syncthreads();
+            work(si, tile);
+            __syncthreads();
+        }
     }
     // Reduction, four outputs at a time (few registers live): the row groups
     // inside a warp (lanes l, l + L, ...) by a fixed xor tree, then the
@@ -283,21 +386,35 @@ __global__ void __launch_bounds__(kTsmThreads, RA * RB > 16 ? 1 : (KAHAN ? 2 : 4
         const int a = (ll / LB) * RA + x / RB, b = (ll % LB) * RB + x % RB;
         if (a < m && b < k) part[(int64_t)(a * k + b) * nb + blockIdx.x] = red[o];
     }
+    // this block's status word (1: a copy wait ran out), written by every block
+    if (t == 0) status[blockIdx.x] = failed ? 1u : 0u;
 }
 
 // X[a, b] = alpha * (sum over blocks, in order) + beta X[a, b]: one warp per output
 template <class T, bool KAHAN>
 __global__ void k_tsmttsm_final(const Comp *__restrict__ part, int nb, int m, int k, double alpha, double beta,
-                                T *__restrict__ X, int64_t ldx) {
+                                T *__restrict__ X, int64_t ldx, const unsigned *status) {
     const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (e >= m * k) return;  // whole warps leave together
     const Comp *p = part + (int64_t)e * nb;
     Comp acc{0.0, 0.0};
-    for (int bl = lane; bl < nb; bl += 32) {
-        if constexpr (KAHAN)
-            acc = comp_merge(acc, p[bl]);
-        else
-            acc.s += p[bl].s;
+    // the lane's partials in block order, four loads in flight at a time
+    for (int b0 = lane; b0 < nb; b0 += 4 * 32) {
+        Comp v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int bl = b0 + q * 32;
+            v[q] = bl < nb ? p[bl] : Comp{0.0, 0.0};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (b0 + q * 32 < nb) {
+                if constexpr (KAHAN)
+                    acc = comp_merge(acc, v[q]);
+                else
+                    acc.s += v[q].s;
+            }
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -307,11 +424,15 @@ __global__ void k_tsmttsm_final(const Comp *__restrict__ part, int nb, int m, in
         else
             acc.s += o.s;
     }
+    // a tile block that gave up waiting for its copies poisons the result
+    bool bad = false;
+    for (int bl = lane; bl < nb; bl += 32) bad |= status[bl] != 0u;
+    bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
         const int a = e / k, b = e - a * k;
         T *xp = X + (int64_t)a * ldx + b;
         const double old = beta != 0.0 ? (double)*xp : 0.0;
-        *xp = (T)(alpha * (acc.s + acc.c) + beta * old);
+        *xp = bad ? (T)NAN : (T)(alpha * (acc.s + acc.c) + beta * old);
     }
 }
 
@@ -414,21 +535,29 @@ static int run_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *Wd, doubl
     constexpr int L = LA * LB, RR = RA * RB, MPs = LA * RA, KPs = LB * RB;
     const int64_t n = V->nrows;
     const int m = V->ncols, k = Wd->ncols;
-    const int tr = tile_rows((MPs + KPs) * (int)sizeof(T));
-    const size_t smem = std::max<size_t>((size_t)kTsmStages * tr * (MPs + KPs) * sizeof(T), (size_t)L * RR * sizeof(Comp));
+    const int vec = (vec16_ok(V->ptr, V->ld, m, sizeof(T)) ? 1 : 0) | (vec16_ok(Wd->ptr, Wd->ld, k, sizeof(T)) ? 2 : 0);
+    // both blocks dense (rows contiguous, 16-byte multiples, no padding
+    // columns): one bulk copy per tile and block vector
+    const bool bulk = SP_TSM_BULK && vec == 3 && V->ld == m && MPs == m && Wd->ld == k && KPs == k;
+    const int S = bulk ? kTsmBulkStages : kTsmStages;
+    const int tr = tile_rows((MPs + KPs) * (int)sizeof(T), bulk ? kTsmBulkTileBytes : kTsmTileBytes);
+    const size_t smem = std::max<size_t>((size_t)S * tr * (MPs + KPs) * sizeof(T) + (bulk ? S * sizeof(uint64_t) : 0),
+                                         (size_t)L * RR * sizeof(Comp));
     const int64_t ntiles = std::max<int64_t>(1, (n + tr - 1) / tr);
-    if (smem > kTsmSmemMax) return SP_ERR_UNSUPPORTED;  // not reached: tiles hold at most kTsmTileBytes
-    auto kern = k_tsmttsm_tile<T, KAHAN, RA, RB, LA, LB>;
+    if (smem > kTsmSmemMax + 1024) return SP_ERR_UNSUPPORTED;  // not reached: tiles are bounded in bytes
+    auto kern = bulk ? k_tsmttsm_tile<T, KAHAN, RA, RB, LA, LB, true> : k_tsmttsm_tile<T, KAHAN, RA, RB, LA, LB, false>;
+    if (smem > kTsmSmemMax) SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t tpb = 1;
     const int nb = tsm_grid(kern, smem, ntiles, &tpb);
     Tmp part(s);  // stream-ordered: no device-wide synchronisation per call
-    SP_TRY(part.alloc((size_t)nb * m * k * sizeof(Comp)));
-    const int vec = (vec16_ok(V->ptr, V->ld, m, sizeof(T)) ? 1 : 0) | (vec16_ok(Wd->ptr, Wd->ld, k, sizeof(T)) ? 2 : 0);
+    const size_t pbytes = (size_t)nb * m * k * sizeof(Comp);
+    SP_TRY(part.alloc(pbytes + (size_t)nb * sizeof(unsigned)));
+    unsigned *status = reinterpret_cast<unsigned *>(part.as<char>() + pbytes);  // one word per tile block
     kern<<<nb, kTsmThreads, smem, s>>>((const T *)V->ptr, V->ld, (const T *)Wd->ptr, Wd->ld, n, m, k, tr, tpb, vec,
-                                       part.as<Comp>());
+                                       part.as<Comp>(), status);
     const int fin_blocks = (m * k * 32 + 255) / 256;
     k_tsmttsm_final<T, KAHAN><<<fin_blocks, 256, 0, s>>>(part.as<const Comp>(), nb, m, k, alpha, beta, (T *)X->ptr,
-                                                         X->ld);
+                                                         X->ld, status);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
@@ -483,6 +612,8 @@ static bool rowmajor_dev(const sp_dense *d) { return d && d->layout == SP_ROW_MA
 
 int sp_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, double beta, int kahan,
                void *stream) {
+    if (sp::dense_scattered(X) || sp::dense_scattered(V) || sp::dense_scattered(W))
+        return sp::scattered_refused("sp_tsmttsm");
     if (!rowmajor_dev(X) || !rowmajor_dev(V) || !rowmajor_dev(W)) return SP_ERR_ARG;
     if (V->nrows != W->nrows || X->nrows != V->ncols || X->ncols != W->ncols) return SP_ERR_DIM;
     if (V->dtype != W->dtype || X->dtype != V->dtype || (V->dtype != SP_F64 && V->dtype != SP_F32))
@@ -499,6 +630,7 @@ int sp_tsmttsm(sp_dense *X, const sp_dense *V, const sp_dense *W, double alpha, 
 }
 
 int sp_tsmm(sp_dense *W, const sp_dense *V, const sp_dense *X, double alpha, double beta, void *stream) {
+    if (sp::dense_scattered(W) || sp::dense_scattered(V) || sp::dense_scattered(X)) return sp::scattered_refused("sp_tsmm");
     if (!rowmajor_dev(X) || !rowmajor_dev(V) || !rowmajor_dev(W)) return SP_ERR_ARG;
     if (V->nrows != W->nrows || X->nrows != V->ncols || X->ncols != W->ncols) return SP_ERR_DIM;
     if (V->dtype != W->dtype || X->dtype != V->dtype || (V->dtype != SP_F64 && V->dtype != SP_F32))

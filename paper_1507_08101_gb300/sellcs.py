@@ -100,6 +100,10 @@ _SIGS = {
     "sp_dense_view_cols": (I, [PP, P, I32, I32]),
     "sp_dense_data": (I, [P, PP, ct.POINTER(I64), ct.POINTER(I32), ct.POINTER(I64), ct.POINTER(I), ct.POINTER(I)]),
     "sp_dense_destroy": (I, [P, P]),
+    "sp_dense_view_scattered": (I, [PP, P, I32, P]),
+    "sp_dense_columns": (I, [P, P]),
+    "sp_dense_clone": (I, [PP, P, I, P]),
+    "sp_dense_copy": (I, [P, P, P]),
     "sp_spmv": (I, [P, P, P, ct.POINTER(sp_spmv_opts), P]),
     "sp_spmv_adjoint": (I, [P, P, P, P, P, P]),
     "sp_batch_create": (I, [PP, I, P, P, P, I, P]),
@@ -120,6 +124,18 @@ _SIGS = {
     "sp_spmv_host": (I, [P, P, P, P, P, P, P, ct.POINTER(sp_spmv_opts)]),
     "sp_host_plan_sync": (I, [P]),
     "sp_host_plan_destroy": (I, [P]),
+    "sp_dist_partition": (I, [I64, P, I, P, I, P]),
+    "sp_dist_plan_create": (I, [PP, I64, I, P, I, P, P]),
+    "sp_dist_plan_info": (I, [P, P, P, P, P, P]),
+    "sp_dist_plan_halo": (I, [P, P, P]),
+    "sp_dist_plan_columns": (I, [P, P]),
+    "sp_dist_plan_split": (I, [P, P, P, P, P, P, P, P]),
+    "sp_dist_plan_set_sends": (I, [P, P, P]),
+    "sp_dist_plan_sends": (I, [P, P, P]),
+    "sp_dist_plan_destroy": (I, [P]),
+    "sp_dist_pack": (I, [P, P, P, P]),
+    "sp_dist_split_opts": (I, [ct.POINTER(sp_spmv_opts), ct.POINTER(sp_spmv_opts), ct.POINTER(sp_spmv_opts)]),
+    "sp_dist_spmv": (I, [P, P, P, P, ct.POINTER(sp_spmv_opts), P, P]),
 }
 
 

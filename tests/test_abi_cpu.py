@@ -98,3 +98,32 @@ def test_host_argument_checks(L):
     assert L.sp_dense_destroy(v, None) == 0
     assert L.sp_dense_destroy(h, None) == 0
     assert L.sp_spmv(None, None, None, None, None) == s.SP_ERR_ARG
+
+
+def test_scattered_view_arguments_without_gpu(L):
+    """Scattered views are host bookkeeping: their checks need no device."""
+    import numpy as np
+    from paper_1507_08101_gb300 import sellcs as s
+    base = ct.c_void_p()
+    assert L.sp_dense_view(ct.byref(base), ct.c_void_p(4096), 10, 6, 6, s.SP_F64, s.SP_ROW_MAJOR) == s.SP_OK
+    v = ct.c_void_p()
+    bad = np.array([1, 6], np.int32)
+    assert L.sp_dense_view_scattered(ct.byref(v), base, 2, s._ptr(bad)) == s.SP_ERR_DIM
+    rep = np.array([1, 1], np.int32)
+    assert L.sp_dense_view_scattered(ct.byref(v), base, 2, s._ptr(rep)) == s.SP_ERR_ARG
+    cols = np.array([5, 1, 3], np.int32)
+    assert L.sp_dense_view_scattered(ct.byref(v), base, 3, s._ptr(cols)) == s.SP_OK
+    got = np.empty(3, np.int32)
+    assert L.sp_dense_columns(v, s._ptr(got)) == 1
+    assert got.tolist() == [5, 1, 3]
+    # a run of a scattered view, and a scattered view of a scattered view
+    r = ct.c_void_p()
+    assert L.sp_dense_view_cols(ct.byref(r), v, 1, 2) == s.SP_OK
+    assert L.sp_dense_columns(r, s._ptr(got[:2])) == 1 and got[:2].tolist() == [1, 3]
+    q = ct.c_void_p()
+    sel = np.array([2, 0], np.int32)
+    assert L.sp_dense_view_scattered(ct.byref(q), v, 2, s._ptr(sel)) == s.SP_OK
+    assert L.sp_dense_columns(q, s._ptr(got[:2])) == 1 and got[:2].tolist() == [3, 5]
+    assert L.sp_dense_columns(base, None) == 0
+    for h in (q, r, v, base):
+        L.sp_dense_destroy(h, None)

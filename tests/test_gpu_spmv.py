@@ -17,6 +17,7 @@ from paper_1507_08101_gb300 import sellcs
 from tests.gpu_helpers import run_case, to_dev
 from tests.test_oracle_format import random_csr
 from workloads import generators as gen
+from workloads.generators import CSR
 
 pytestmark = pytest.mark.gpu
 
@@ -72,8 +73,13 @@ def test_rectangular(cuda_ok):
     A = random_csr(300, 517, 0.05, rng)
     for w in (1, 4, 9):
         run_case(A, 16, 64, w, {"scale", "axpby", "chain", "dot_yy"}, seed=w)
+    # more columns than rows: the shift and the x-dots use x's first nrows
+    # rows (a process's rows with its halo columns appended)
+    run_case(A, 16, 64, 2, {"scale", "shift", "dot_xy", "dot_xx", "dot_yy"}, seed=11)
+    run_case(A, 32, 1, 3, {"vshift", "axpby", "dot_xy"}, seed=12)
+    B = random_csr(517, 300, 0.05, rng)
     with pytest.raises(sellcs.SpError) as e:
-        run_case(A, 16, 64, 2, {"dot_xy"})
+        run_case(B, 16, 64, 2, {"dot_xy"})
     assert e.value.code == sellcs.SP_ERR_DIM
 
 
@@ -242,3 +248,30 @@ def test_float64_extreme_magnitudes(cuda_ok):
     fin = np.isfinite(yr)
     s = orc.spmmv_scale(A, np.where(np.isfinite(X), X, 0.0))
     assert np.all(np.abs(yg[fin] - yr[fin]) <= 1e-12 * s[fin] + 1e-300)
+
+
+@pytest.mark.parametrize("C,sigma", [(32, 1), (32, 32), (32, 256), (64, 64), (64, 1)])
+def test_lockstep_rows_exact_tail(cuda_ok, C, sigma):
+    """Single float64 vectors with widely spread row lengths take the lockstep
+    row loop, whose last steps stop at the chunk's longest row (a jump into
+    the unrolled sequence).  Rows of every length from 0 to 90 (every tail
+    length), padding rows in the last chunk (N = 32 k + 5): y, z and the dots
+    against the oracle, for every work order, bit-identical between the
+    orders."""
+    rng = np.random.default_rng(C + sigma)
+    N = 32 * 97 + 5
+    lens = rng.integers(0, 91, N)
+    lens[rng.random(N) < 0.1] = 0
+    rowptr = np.zeros(N + 1, np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    col = np.concatenate([np.sort(rng.choice(N, int(k), replace=False)) for k in lens]).astype(np.int32)
+    A = CSR(N, N, rowptr, col, rng.uniform(-1, 1, int(rowptr[-1])))
+    ys = []
+    for order in ("auto", "front", "ranges"):
+        m = sellcs.SellMatrix(A, C=C, sigma=sigma, order=order)
+        y, _, _ = run_case(A, C, sigma, 1, {"scale", "shift", "axpby", "dot_yy", "dot_xy", "chain"}, mat=m, seed=3)
+        run_case(A, C, sigma, 1, set(), mat=m, seed=4)
+        run_case(A, C, sigma, 1, {"scale", "axpby"}, mat=m, seed=5)
+        m.close()
+        ys.append(y)
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])

@@ -92,5 +92,12 @@ def test_tsm_argument_errors(cuda_ok):
     with pytest.raises(sellcs.SpError):
         sellcs.tsmttsm(torch.zeros(3, 4, dtype=torch.float64, device="cuda"), W, W)  # X shape
     Vs = torch.zeros(10, 4, dtype=torch.float64, device="cuda")
-    with pytest.raises(sellcs.SpError):
-        sellcs.tsmm(Vs[:, :3], Vs, torch.zeros(4, 3, dtype=torch.float64, device="cuda"))  # partial overlap
+    with pytest.raises(sellcs.SpError) as e:
+        # W a narrower view of V at the same address: not the in-place form (m != k)
+        sellcs.tsmm(Vs[:, :3], Vs, torch.zeros(4, 3, dtype=torch.float64, device="cuda"))
+    assert e.value.code == sellcs.SP_ERR_ARG
+    Vb = torch.zeros(12, 4, dtype=torch.float64, device="cuda")
+    with pytest.raises(sellcs.SpError) as e:
+        # same leading dimension, rows shifted by two: a partial overlap
+        sellcs.tsmm(Vb[2:], Vb[:10], torch.zeros(4, 4, dtype=torch.float64, device="cuda"))
+    assert e.value.code == sellcs.SP_ERR_ARG

@@ -164,3 +164,24 @@ def test_round_values_bf16_and_f32():
     # ties to even at 1.0: spacing 2**-7
     r = oracle.round_values(np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8]), "bf16")
     assert r[0] == 1.0 and r[1] == 1 + 2 ** -6
+
+
+def test_openmp_timing_variant_matches_single_thread():
+    """The all-cores timing baseline (orc_spmmv_omp) computes every row as
+    orc_spmmv does: the same y and z bits; the dots differ only by the order
+    in which the threads' compensated sums are added."""
+    from workloads import generators as gen
+    A = gen.irregular_band(3001, lmin=0, lmax=40, band=200, seed=3)
+    rng = np.random.default_rng(0)
+    X, Y0, Z0 = (rng.uniform(-1, 1, (A.nrows, 2)) for _ in range(3))
+    kw = dict(alpha=0.5, gamma=[0.1, -0.2], beta=1.0, y0=Y0, dot_yy=True, dot_xy=True, dot_xx=True, delta=0.9,
+              eta=0.1, z0=Z0)
+    yr, dr, zr = oracle.spmmv(A, X, **kw)
+    for nt in (1, 3, 8):
+        got = oracle.spmmv_omp(A, X, nthreads=nt, **kw)
+        if got is None:
+            pytest.skip("gcc without OpenMP")
+        y, d, z = got
+        np.testing.assert_array_equal(y, yr)
+        np.testing.assert_array_equal(z, zr)
+        np.testing.assert_allclose(d, dr, rtol=1e-15, atol=0)
