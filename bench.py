@@ -77,6 +77,21 @@ def measured_fp64_rate():
     return out
 
 
+def fp64_derived_peak(meas):
+    """Float64 peak from the unit count and the clock: 2 fused multiply-adds
+    per SM and cycle (one float64 warp instruction about every 16 SM cycles)
+    x SMs x the maximum SM clock x 2 flops.  The DFMA-chain micro-benchmark
+    (sp_device_fp64_rate) reaches about 0.85 of it, below what the float64
+    tall-skinny product sustains (0.95), so it is reported beside the derived
+    figure rather than used as the ceiling."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (meas.get("clocks") or {}).get("sm_max_mhz") or 2070.0
+    peak = 2 * 2 * sms * mhz * 1e6 / 1e12
+    return round(peak, 4), (f"derived: 2 float64 fma per SM per cycle x {sms} SMs x {mhz:.0f} MHz x 2 flops; "
+                            f"measured DFMA-chain rate {meas['tflops']} TFLOP/s beside it")
+
+
 def fp64_flops(nnz, nrows, w, shift, scale, axpby, ndots, chain):
     """float64 flops of one call: the row sums (2 per nonzero and column) and
     the epilogue per row and column (fma = 2, mul = 1)."""
@@ -324,7 +339,7 @@ def run_ours(args, rank, world):
     flops = fp64_flops(A.nnz, A.nrows, 1, True, True, True, 2, True)
     tflops = flops / (ms_step * 1e-3) / 1e12
     fp64 = measured_fp64_rate()
-    fp64_peak = fp64["tflops"]
+    fp64_peak, fp64_kind = fp64_derived_peak(fp64)
     hbm = {"bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
            "peak_kind": f"{peak_kind} copy bandwidth (burst)",
            "traffic": recorded_traffic("k_spmmv_irregular_augmented.md"),
@@ -332,8 +347,7 @@ def run_ours(args, rank, world):
            "algorithmic_bytes_per_launch": nbytes}
     alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": fp64_peak, "unit": "TFLOP/s",
            "frac": round(tflops / fp64_peak, 4),
-           "peak_kind": "measured float64 fma rate of this GPU (sp_device_fp64_rate; nominal 1.25 TFLOP/s)",
-           "fp64_flops_per_launch": flops, "fp64_rate_measurement": fp64}
+           "peak_kind": fp64_kind, "fp64_flops_per_launch": flops, "fp64_rate_measurement": fp64}
     # the binding resource is the one closest to its ceiling; the other is reported beside it
     roof = dict(alu if alu["frac"] > hbm["frac"] else hbm)
     roof["other"] = hbm if roof["bound"] == "alu" else alu
