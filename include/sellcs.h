@@ -270,6 +270,31 @@ typedef struct {
  */
 SP_API int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts *opts, void *stream);
 
+/*
+ * The augmented product fused with the inner products of a tall and skinny
+ * block V with the new y (the dense-matrix section's X = V^T W, here with
+ * W = y, formed while y is written; for block orthogonalisation after a
+ * product, the step the paper's block solvers pair with the SpMMV):
+ *     y = alpha (A - gamma I) x + beta y  [z = delta z + eta y],  C = V^T y
+ *   y, x, z, opts  as sp_spmv, with SCALE, SHIFT, VSHIFT, AXPBY and
+ *                  CHAIN_AXPBY (the fused dots are refused: SP_ERR_ARG);
+ *                  float64 values and vectors, row-major, w <= 8, each row a
+ *                  whole number of the kernel's lane vectors and aligned to
+ *                  them (else SP_ERR_UNSUPPORTED), and the matrix's chunk
+ *                  height at least 32 / (lanes per row) (rows are not split
+ *                  over lanes here; else SP_ERR_UNSUPPORTED); not for
+ *                  SP_MAT_PERMUTED_SPACE
+ *   V              nrows x m, float64, row-major, 1 <= m <= 8; must not
+ *                  overlap y or z
+ *   C              device, m x w float64, row-major with leading dimension
+ *                  ldc >= w, overwritten with V^T y (the new y)
+ * The sums of C are deterministic (fixed lane tree, warps and blocks in
+ * order).  Shares the matrix's reduction scratch with sp_spmv's dots: calls
+ * on one matrix must be ordered.  Asynchronous.
+ */
+SP_API int sp_spmv_vty(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts *opts, const sp_dense *V,
+                       double *C, int64_t ldc, void *stream);
+
 /* ------------------------------------------------------------------ derivatives */
 
 /*

@@ -12,6 +12,8 @@
 namespace sp {
 template <class VT, class XT>
 int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
+int launch_spmv_vty(const SpmvArgs &a, const double *V, int64_t ldv, int m, double *C, int64_t ldc, int max_blocks,
+                    cudaStream_t s);
 int spmv_scattered(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts &o, void *stream);
 }
 
@@ -623,6 +625,83 @@ int sp_spmv(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts 
         SP_CUDA(cudaStreamSynchronize(s));
     }
     return SP_OK;
+}
+
+int sp_spmv_vty(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts *opts, const sp_dense *V,
+                double *C, int64_t ldc, void *stream) {
+    static const sp_spmv_opts defaults = SP_SPMV_OPTS_INIT;
+    if (!y || !A || !x || !V || !C) return SP_ERR_ARG;
+    const sp_spmv_opts &o = opts ? *opts : defaults;
+    const uint32_t f = o.flags;
+    const uint32_t known = SP_SPMV_SCALE | SP_SPMV_SHIFT | SP_SPMV_VSHIFT | SP_SPMV_AXPBY | SP_SPMV_CHAIN_AXPBY;
+    if (f & ~known) return SP_ERR_ARG;  // the fused dots are not combined with V^T y here
+    if (dense_scattered(x) || dense_scattered(y) || dense_scattered(V) ||
+        ((f & SP_SPMV_CHAIN_AXPBY) && dense_scattered(o.z)))
+        return scattered_refused("sp_spmv_vty");
+    const Pattern &P = *A->pat;
+    if (P.permuted_space) return SP_ERR_ARG;
+    if (A->vdt != SP_F64 || x->dtype != SP_F64 || y->dtype != SP_F64 || V->dtype != SP_F64) return SP_ERR_DTYPE;
+    if (x->layout != SP_ROW_MAJOR || y->layout != SP_ROW_MAJOR || V->layout != SP_ROW_MAJOR) return SP_ERR_ARG;
+    if (x->nrows != P.ncols || y->nrows != P.nrows || x->ncols != y->ncols || V->nrows != y->nrows)
+        return SP_ERR_DIM;
+    const int w = x->ncols, m = V->ncols;
+    if (w < 1 || w > 8 || m < 1 || m > 8) return SP_ERR_UNSUPPORTED;
+    if (ldc < w) return SP_ERR_DIM;
+    const bool shift = f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT);
+    if ((f & SP_SPMV_SHIFT) && (f & SP_SPMV_VSHIFT)) return SP_ERR_ARG;
+    if (shift && !o.gamma) return SP_ERR_ARG;
+    if (shift && P.ncols < P.nrows) return SP_ERR_DIM;
+    const bool chain = f & SP_SPMV_CHAIN_AXPBY;
+    if (chain) {
+        if (!o.z) return SP_ERR_ARG;
+        if (o.z->nrows != y->nrows || o.z->ncols != w) return SP_ERR_DIM;
+        if (o.z->dtype != SP_F64 || o.z->layout != SP_ROW_MAJOR) return SP_ERR_ARG;
+        if (overlap(o.z, x) || overlap(o.z, y) || overlap(o.z, V)) return SP_ERR_ARG;
+    }
+    if (overlap(x, y) || overlap(V, y)) return SP_ERR_ARG;
+    // vector loads of whole rows: rows a multiple of the lane vector, aligned
+    const int cpl = host_cols_per_lane(8, w);
+    const size_t align = std::min<size_t>(16, (size_t)cpl * 8);
+    auto ok = [&](const sp_dense *d) { return ((uintptr_t)d->ptr % align) == 0 && ((size_t)d->ld * 8) % align == 0; };
+    if (w % cpl != 0 || !ok(x) || !ok(y) || (chain && !ok(o.z))) return SP_ERR_UNSUPPORTED;
+    int wp = 1;
+    while (wp < w) wp <<= 1;
+    if (host_log2_tpr(P.C, wp / cpl) != 0) return SP_ERR_UNSUPPORTED;  // rows split over lanes: not here
+    if (!A->scratch) return SP_ERR_ARG;
+    SpmvArgs a{};
+    a.val = A->val->ptr;
+    a.col = (const int32_t *)P.col->ptr;
+    a.chunkptr = (const int64_t *)P.chunkptr->ptr;
+    a.chunklen = (const int32_t *)P.chunklen->ptr;
+    a.slotlen = (const int32_t *)P.slotlen->ptr;
+    a.perm = P.sigma == 1 ? nullptr : (const int32_t *)P.perm->ptr;
+    a.nrows = P.nrows;
+    a.nslots = P.nslots;
+    a.C = P.C;
+    a.w = w;
+    a.x = x->ptr;
+    a.xrs = x->ld;
+    a.xcs = 1;
+    a.y = y->ptr;
+    a.yrs = y->ld;
+    a.ycs = 1;
+    a.z = chain ? o.z->ptr : nullptr;
+    a.zrs = chain ? o.z->ld : 0;
+    a.zcs = 1;
+    a.flags = f;
+    a.alpha = o.alpha;
+    a.beta = o.beta;
+    a.delta = o.delta;
+    a.eta = o.eta;
+    a.partials = (double *)A->scratch->ptr;
+    a.ticket = (unsigned *)((char *)A->scratch->ptr + A->scratch_bytes - 256);
+    for (int k = 0; k < kMaxTileW; ++k)
+        a.gamma[k] = !shift || k >= w ? 0.0 : ((f & SP_SPMV_SHIFT) ? o.gamma[0] : o.gamma[k]);
+    if (P.nrows == 0) {
+        SP_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)ldc * m, (cudaStream_t)stream));
+        return SP_OK;
+    }
+    return launch_spmv_vty(a, (const double *)V->ptr, V->ld, m, C, ldc, max_blocks_of(A), (cudaStream_t)stream);
 }
 
 int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,

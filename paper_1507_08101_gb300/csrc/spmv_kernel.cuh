@@ -305,6 +305,16 @@ __device__ __forceinline__ void load_out(const XT *p, int64_t cs, int nvalid, XT
     }
 }
 
+// SP_STORE_CS: 1 = outputs (y, z) are stored with the streaming hint
+// (evict-first), so that written rows do not push x out of L2
+#ifndef SP_STORE_CS
+#define SP_STORE_CS 0
+#endif
+template <class T>
+__device__ __forceinline__ void st_out(T *p, T v) {
+    if constexpr (SP_STORE_CS != 0) __stcs(p, v);
+    else *p = v;
+}
 template <class XT, int CPL, bool VEC>
 __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const XT (&o)[CPL]) {
     if constexpr (VEC) {
@@ -314,19 +324,19 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
             for (int q = 0; q < B / 16; ++q) {
                 uint4 u;
                 memcpy(&u, &o[q * (16 / sizeof(XT))], 16);
-                reinterpret_cast<uint4 *>(p)[q] = u;
+                st_out(reinterpret_cast<uint4 *>(p) + q, u);
             }
         } else if constexpr (B == 8) {
             uint2 u;
             memcpy(&u, &o[0], 8);
-            *reinterpret_cast<uint2 *>(p) = u;
+            st_out(reinterpret_cast<uint2 *>(p), u);
         } else {
-            *p = o[0];
+            st_out(p, o[0]);
         }
     } else {
 #pragma unroll
         for (int c = 0; c < CPL; ++c)
-            if (c < nvalid) p[c * cs] = o[c];
+            if (c < nvalid) st_out(p + c * cs, o[c]);
     }
 }
 

@@ -106,6 +106,7 @@ _SIGS = {
     "sp_dense_copy": (I, [P, P, P]),
     "sp_spmv": (I, [P, P, P, ct.POINTER(sp_spmv_opts), P]),
     "sp_spmv_adjoint": (I, [P, P, P, P, P, P]),
+    "sp_spmv_vty": (I, [P, P, P, ct.POINTER(sp_spmv_opts), P, P, I64, P]),
     "sp_batch_create": (I, [PP, I, P, P, P, I, P]),
     "sp_batch_bind": (I, [P, P, P, P, P]),
     "sp_batch_spmv": (I, [P, ct.c_uint32, ct.c_double, ct.c_double, P, P]),
@@ -439,6 +440,27 @@ def spmv(A: SellMatrix, x, y, *, alpha=None, gamma=None, beta=None, dot_yy=False
         if hz is not None:
             L.sp_dense_destroy(hz, None)
     return dot
+
+
+def spmv_vty(A: SellMatrix, x, y, V, C, *, alpha=None, gamma=None, beta=None, z=None, delta=None, eta=None,
+             stream=None):
+    """y = alpha (A - gamma I) x + beta y (+ z = delta z + eta y) and C = V^T y
+    in one pass (sp_spmv_vty); x, y, z: CUDA float64 (n,) or (n, w); V: (n, m);
+    C: CUDA float64 (m, w) written.  Returns C."""
+    L = lib()
+    hx, hy, hv = sp_dense_view(x), sp_dense_view(y), sp_dense_view(V if V.dim() == 2 else V[:, None])
+    hz = sp_dense_view(z) if z is not None else None
+    w = 1 if x.dim() == 1 else x.shape[1]
+    try:
+        o, keep = make_opts(w, alpha=alpha, gamma=gamma, beta=beta, z_handle=hz, delta=delta, eta=eta)
+        ldc = C.stride(0) if C.dim() == 2 else 1
+        check(L.sp_spmv_vty(hy, A.handle, hx, ct.byref(o), hv, _ptr(C), int(max(ldc, w)), _stream(stream)),
+              "sp_spmv_vty")
+    finally:
+        for h in (hx, hy, hv, hz):
+            if h is not None:
+                L.sp_dense_destroy(h, None)
+    return C
 
 
 def mat_permute(A: SellMatrix, out, inp, to_sell: bool, stream=None):
