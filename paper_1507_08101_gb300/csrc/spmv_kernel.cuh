@@ -305,17 +305,22 @@ __device__ __forceinline__ void load_out(const XT *p, int64_t cs, int nvalid, XT
     }
 }
 
-// SP_STORE_CS: 1 = outputs (y, z) are stored with the streaming hint
-// (evict-first), so that written rows do not push x out of L2
+// CS: store with the streaming hint (evict-first), for an output the call
+// does not read again, so that written rows do not push x out of L2 (plain
+// float64 product, Laplacian 256^3: 328 -> 314 us); SP_STORE_CS forces it on
+// for every output (a knob)
 #ifndef SP_STORE_CS
 #define SP_STORE_CS 0
 #endif
-template <class T>
+#ifndef SP_STORE_CS_PLAIN
+#define SP_STORE_CS_PLAIN 1
+#endif
+template <bool CS, class T>
 __device__ __forceinline__ void st_out(T *p, T v) {
-    if constexpr (SP_STORE_CS != 0) __stcs(p, v);
+    if constexpr (CS || SP_STORE_CS != 0) __stcs(p, v);
     else *p = v;
 }
-template <class XT, int CPL, bool VEC>
+template <class XT, int CPL, bool VEC, bool CS = false>
 __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const XT (&o)[CPL]) {
     if constexpr (VEC) {
         constexpr int B = CPL * (int)sizeof(XT);
@@ -324,19 +329,19 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
             for (int q = 0; q < B / 16; ++q) {
                 uint4 u;
                 memcpy(&u, &o[q * (16 / sizeof(XT))], 16);
-                st_out(reinterpret_cast<uint4 *>(p) + q, u);
+                st_out<CS>(reinterpret_cast<uint4 *>(p) + q, u);
             }
         } else if constexpr (B == 8) {
             uint2 u;
             memcpy(&u, &o[0], 8);
-            st_out(reinterpret_cast<uint2 *>(p), u);
+            st_out<CS>(reinterpret_cast<uint2 *>(p), u);
         } else {
-            st_out(p, o[0]);
+            st_out<CS>(p, o[0]);
         }
     } else {
 #pragma unroll
         for (int c = 0; c < CPL; ++c)
-            if (c < nvalid) st_out(p + c * cs, o[c]);
+            if (c < nvalid) st_out<CS>(p + c * cs, o[c]);
     }
 }
 
@@ -584,6 +589,9 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 #ifndef SP_PREFETCH_META_F32
 #define SP_PREFETCH_META_F32 1
 #endif
+#ifndef SP_PREFETCH_META_F64_PLAIN
+#define SP_PREFETCH_META_F64_PLAIN 0
+#endif
 
 // MT: rows may be split over T > 1 lanes (threads per row).  With MT false the
 // kernel is compiled for T = 1 and carries none of the split-row logic.
@@ -591,8 +599,10 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 // the launcher uses 0, 3 (the pair of the bench product and of the KPM steps)
 // or 7, and the flags pick which of them are written.
 // EPI: the epilogue's arithmetic, fixed at compile time where the float64
-// pipe binds (float64 vectors without dots): 0 y = t; 1 y = alpha t + beta y
-// (the Chebyshev step); 2 every augmentation by its runtime flag.  A runtime
+// pipe binds (float64 vectors): 0 y = t; 1 y = alpha t + beta y (the
+// Chebyshev step); 2 every augmentation by its runtime flag; 3 shift, scale
+// and beta = 1 (dots and chain by their flags): y = alpha t - alpha gamma x_i
+// + y_old in two fused multiply-adds.  A runtime
 // flag that is off still costs: the compiler turns a short conditional into
 // an unconditional operation and a select, and for float64 vectors that
 // operation occupies the float64 pipe (Laplacian 256^3: three of every eleven
@@ -615,7 +625,11 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     constexpr int R = 32 / G;
     constexpr int U = CPL >= 4 ? (sizeof(XT) == 4 ? SP_UNROLL_WIDE_F32 : SP_UNROLL_WIDE) : SP_UNROLL_NARROW / CPL;
     constexpr bool early_epi = sizeof(XT) == 8 ? SP_EARLY_EPI_F64 != 0 : SP_EARLY_EPI_F32 != 0;
-    constexpr bool prefetch_meta = sizeof(XT) == 8 ? SP_PREFETCH_META_F64 != 0 : SP_PREFETCH_META_F32 != 0;
+    // the plain float64 product (no epilogue loads, no dots) has registers to
+    // spare for the next slot's metadata
+    constexpr bool prefetch_meta = sizeof(XT) == 8 ? (EPI == 0 ? SP_PREFETCH_META_F64_PLAIN != 0
+                                                               : SP_PREFETCH_META_F64 != 0)
+                                                   : SP_PREFETCH_META_F32 != 0;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lt = MT ? a.log2_tpr : 0;     // T = 1 << lt lanes per row (runtime)
@@ -628,11 +642,11 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     const int k0 = gl * CPL;
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const uint32_t f = a.flags;
-    static_assert(EPI == 2 || DM == 0, "compile-time epilogues have no dots");
-    const bool shift = EPI == 2 && (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0;
-    const bool do_scale = EPI == 2 ? (f & SP_SPMV_SCALE) != 0 : EPI == 1;
-    const bool do_axpby = EPI == 2 ? (f & SP_SPMV_AXPBY) != 0 : EPI == 1;
-    const bool do_chain = EPI == 2 && (f & SP_SPMV_CHAIN_AXPBY) != 0;
+    static_assert(EPI >= 2 || DM == 0, "compile-time epilogues 0 and 1 have no dots");
+    const bool shift = EPI == 3 || (EPI == 2 && (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0);
+    const bool do_scale = EPI == 2 ? (f & SP_SPMV_SCALE) != 0 : EPI != 0;
+    const bool do_axpby = EPI == 2 ? (f & SP_SPMV_AXPBY) != 0 : EPI != 0;
+    const bool do_chain = EPI >= 2 && (f & SP_SPMV_CHAIN_AXPBY) != 0;
     const bool need_xi = shift || (DM != 0 && (f & (SP_SPMV_DOT_XY | SP_SPMV_DOT_XX)));
     const VT *__restrict__ val = (const VT *)a.val;
     const XT *__restrict__ x = (const XT *)a.x;
@@ -642,6 +656,13 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     XT gam[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) gam[c] = (shift && k0 + c < a.w) ? (XT)a.gamma[k0 + c] : XT(0);
+    if constexpr (EPI == 3) {
+        // beta = 1: y = alpha t - (alpha gamma) x_i + y_old as two fused
+        // multiply-adds (one float64 instruction per row fewer than
+        // alpha (t - gamma x_i) + beta y_old)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) gam[c] = mul_rn(alpha, gam[c]);
+    }
 
     DT dyy[(DM & 1) ? CPL : 1], dxy[(DM & 2) ? CPL : 1], dxx[(DM & 4) ? CPL : 1];
 #pragma unroll
@@ -761,12 +782,20 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             XT v = rs[c];
-            if (shift) v = fma_rn(-gam[c], xi[c], v);
-            if (do_scale) v = mul_rn(alpha, v);
-            if (do_axpby) v = fma_rn(beta, yo[c], v);
+            if constexpr (EPI == 3) {
+                v = fma_rn(alpha, v, fma_rn(-gam[c], xi[c], yo[c]));
+            } else {
+                if (shift) v = fma_rn(-gam[c], xi[c], v);
+                if (do_scale) v = mul_rn(alpha, v);
+                if (do_axpby) v = fma_rn(beta, yo[c], v);
+            }
             t[c] = v;
         }
-        store_out<XT, CPL, VEC>(yp, a.ycs, nvalid, t);
+        // without the beta term y is not read by this call: streaming stores
+        if (SP_STORE_CS_PLAIN != 0 && !do_axpby)
+            store_out<XT, CPL, VEC, true>(yp, a.ycs, nvalid, t);
+        else
+            store_out<XT, CPL, VEC, false>(yp, a.ycs, nvalid, t);
         if constexpr (DOTS) {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {

@@ -85,6 +85,17 @@ template <class VT, class XT, int WP, bool MT, bool LS>
 static int launch_spmv_wml(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s) {
     // dot set compiled in: none, <y,y> and <x,y>, or all three
     const uint32_t req = (a.flags & SP_SPMV_DOT_ANY) / SP_SPMV_DOT_YY;
+    if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+        // shift, scale and beta = 1 with fused dots: the two-fma epilogue
+        const uint32_t need = SP_SPMV_SCALE | SP_SPMV_AXPBY;
+        if (req && (a.flags & need) == need && (a.flags & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) && a.beta == 1.0) {
+            if (req & 4)
+                return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS, 3>(a, max_blocks, s)
+                           : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS, 3>(a, max_blocks, s);
+            return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS, 3>(a, max_blocks, s)
+                       : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS, 3>(a, max_blocks, s);
+        }
+    }
     if (req & 4)
         return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS, 2>(a, max_blocks, s)
                    : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS, 2>(a, max_blocks, s);
