@@ -656,13 +656,6 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     XT gam[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) gam[c] = (shift && k0 + c < a.w) ? (XT)a.gamma[k0 + c] : XT(0);
-    if constexpr (EPI == 3) {
-        // beta = 1: y = alpha t - (alpha gamma) x_i + y_old as two fused
-        // multiply-adds (one float64 instruction per row fewer than
-        // alpha (t - gamma x_i) + beta y_old)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) gam[c] = mul_rn(alpha, gam[c]);
-    }
 
     DT dyy[(DM & 1) ? CPL : 1], dxy[(DM & 2) ? CPL : 1], dxx[(DM & 4) ? CPL : 1];
 #pragma unroll
@@ -783,6 +776,9 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         for (int c = 0; c < CPL; ++c) {
             XT v = rs[c];
             if constexpr (EPI == 3) {
+                // beta = 1: y = alpha t - (alpha gamma) x_i + y_old as two fused
+                // multiply-adds; the launcher passes alpha gamma (rounded once
+                // on the host) in place of gamma
                 v = fma_rn(alpha, v, fma_rn(-gam[c], xi[c], yo[c]));
             } else {
                 if (shift) v = fma_rn(-gam[c], xi[c], v);

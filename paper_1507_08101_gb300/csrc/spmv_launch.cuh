@@ -89,11 +89,13 @@ static int launch_spmv_wml(const SpmvArgs &a, bool vec, int max_blocks, cudaStre
         // shift, scale and beta = 1 with fused dots: the two-fma epilogue
         const uint32_t need = SP_SPMV_SCALE | SP_SPMV_AXPBY;
         if (req && (a.flags & need) == need && (a.flags & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) && a.beta == 1.0) {
+            SpmvArgs b = a;  // the kernel takes alpha gamma in place of gamma
+            for (int k = 0; k < kMaxTileW; ++k) b.gamma[k] = a.alpha * a.gamma[k];
             if (req & 4)
-                return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS, 3>(a, max_blocks, s)
-                           : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS, 3>(a, max_blocks, s);
-            return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS, 3>(a, max_blocks, s)
-                       : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS, 3>(a, max_blocks, s);
+                return vec ? launch_spmv_variant<VT, XT, WP, true, 7, MT, LS, 3>(b, max_blocks, s)
+                           : launch_spmv_variant<VT, XT, WP, false, 7, MT, LS, 3>(b, max_blocks, s);
+            return vec ? launch_spmv_variant<VT, XT, WP, true, 3, MT, LS, 3>(b, max_blocks, s)
+                       : launch_spmv_variant<VT, XT, WP, false, 3, MT, LS, 3>(b, max_blocks, s);
         }
     }
     if (req & 4)
