@@ -126,4 +126,4 @@ def test_empty_part_and_no_halo(cuda_ok):
     yr, dr, zr = oracle.spmmv(A, X, alpha=0.5, beta=1.0, y0=Y0, dot_yy=True, delta=0.5, eta=1.0, z0=Z0)
     np.testing.assert_array_equal(y, yr)  # y = x + y0 exactly: 0.5 * 2 x + y0
     assert_close(z, zr, np.abs(zr) + 1, 1e-15, "z")
-    assert abs(d[0] - dr[0]) <= 1e-13 * abs(dr[0])
+    assert_close(d[:1], dr[:1], dot_bound("dot_yy", yr, X, 1e-12 * np.abs(yr), "f64", n + 3), 1.0, "dot_yy")

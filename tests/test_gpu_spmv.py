@@ -14,7 +14,7 @@ import torch
 
 import oracle
 from paper_1507_08101_gb300 import sellcs
-from tests.gpu_helpers import run_case, to_dev
+from tests.gpu_helpers import assert_close, dot_bound, run_case, to_dev
 from tests.test_oracle_format import random_csr
 from workloads import generators as gen
 from workloads.generators import CSR
@@ -170,8 +170,10 @@ def test_dot_to_host_pointer(cuda_ok, irregular):
                                dot_host=True)
     sellcs.check(sellcs.lib().sp_spmv(hy, mat.handle, hx, ct.byref(o), sellcs._stream(None)), "spmv")
     yr, dr, _ = oracle.spmmv(irregular, X, dot_yy=True, dot_xx=True)
-    np.testing.assert_allclose(host[6:], dr[6:], rtol=1e-13)
-    np.testing.assert_allclose(host[:3], dr[:3], rtol=1e-12)
+    e = 1e-12 * oracle.spmmv_scale(irregular, X)
+    N = irregular.nrows
+    assert_close(host[6:], dr[6:], dot_bound("dot_xx", yr, X, e, "f64", N), 1.0, "host dot_xx")
+    assert_close(host[:3], dr[:3], dot_bound("dot_yy", yr, X, e, "f64", N), 1.0, "host dot_yy")
     assert np.all(np.isnan(host[3:6]))
     sellcs.sp_dense_destroy(hx)
     sellcs.sp_dense_destroy(hy)
