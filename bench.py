@@ -593,6 +593,54 @@ def secondary_permuted(peak):
     return out
 
 
+def secondary_vty(peak):
+    """The bench product (irregular N = 2^21, SELL-32-256, f64, w = 1,
+    shift/scale/beta and the chain) fused with C = V^T y for a block V of m
+    columns (sp_spmv_vty), against the same product followed by a separate
+    tall-skinny pass (sp_spmv, then sp_tsmttsm over V and y).  The fused form
+    saves one read of y; both read V once."""
+    import torch
+    from paper_1507_08101_gb300 import sellcs
+    A, X, Y0, Z0 = make_workload()
+    W = WORKLOAD
+    m = sellcs.SellMatrix(A, C=W["C"], sigma=W["sigma"], dtype="f64")
+    inf = m.info()
+    x, y, z = (torch.from_numpy(v).cuda() for v in (X, Y0, Z0))
+    kw = dict(alpha=W["alpha"], gamma=W["gamma"], beta=W["beta"], z=z, delta=W["delta"], eta=W["eta"])
+    nb_prod = algorithmic_bytes(A.nnz, A.nrows, A.ncols, inf["nchunks"], inf["nchunks"] * W["C"], 1, 8, 8, True, True,
+                                W["sigma"] > 1)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for mm in (1, 4, 8):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1000 + mm)
+        V = torch.rand(A.nrows, mm, dtype=torch.float64, device="cuda", generator=g) - 0.5
+        Cf = torch.empty(mm, 1, dtype=torch.float64, device="cuda")
+        Cu = torch.empty(mm, 1, dtype=torch.float64, device="cuda")
+        y2 = y.view(-1, 1)
+
+        def fused():
+            sellcs.spmv_vty(m, x, y, V, Cf, **kw)
+
+        def unfused():
+            sellcs.spmv(m, x, y, **kw)
+            sellcs.tsmttsm(Cu, V, y2)
+
+        for _ in range(5):
+            fused()
+            unfused()
+        torch.cuda.synchronize()
+        tf = _events_time(fused, 100, stream)
+        tu = _events_time(unfused, 100, stream)
+        nb_f = nb_prod + A.nrows * mm * 8
+        nb_u = nb_prod + A.nrows * (mm + 1) * 8
+        out[f"m{mm}"] = {"fused_us": round(tf * 1e3, 1), "fused_GBs": round(nb_f / tf / 1e6, 1),
+                         "unfused_us": round(tu * 1e3, 1), "unfused_GBs_of_its_bytes": round(nb_u / tu / 1e6, 1),
+                         "speedup_fused": round(tu / tf, 3)}
+    m.close()
+    return out
+
+
 def secondary_dist(peak):
     """The row-partitioned product of the bench workload with P parts on this
     one GPU (dist.LocalWorld: every part's halo pack, the halo copies and every
@@ -969,7 +1017,7 @@ def main():
     ap.add_argument("--no-fp64-probe", action="store_true",
                     help="skip the float64 rate probe that runs after the timed region")
     ap.add_argument("--only", choices=["laplace", "laplace256", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm",
-                                       "permuted", "tsm", "fp64_rate", "dist", "layout"],
+                                       "permuted", "tsm", "fp64_rate", "dist", "layout", "vty"],
                     help="run one secondary workload alone and print its JSON")
     ap.add_argument("--pairs", default=None,
                     help="with --only anderson_w16: comma-separated value:vector precision pairs, e.g. f32:f32; "
@@ -995,7 +1043,7 @@ def main():
                "tsm": lambda p: secondary_tsm(p, tuple(args.pairs.split(",")) if args.pairs else ("f64", "f32")),
                "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
                "permuted": secondary_permuted, "dist": secondary_dist,
-               "layout": secondary_layout}
+               "layout": secondary_layout, "vty": secondary_vty}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)
         return
     if world > 1:
@@ -1015,7 +1063,9 @@ def main():
         sec = {}
         for name, fn in (("laplace", secondary_laplace), ("anderson_w16", secondary_anderson),
                          ("powerlaw_adjoint", secondary_powerlaw), ("cg_batch", secondary_cg_batch),
-                         ("kpm", secondary_kpm)):
+                         ("kpm", secondary_kpm), ("vty", secondary_vty),
+                         ("tsm", lambda p: secondary_tsm(p, ("f64", "f32"))), ("layout", secondary_layout),
+                         ("permuted", secondary_permuted), ("dist", secondary_dist)):
             try:
                 sec[name] = fn(peak)
             except Exception as e:  # a failed secondary measurement must not hide the headline
