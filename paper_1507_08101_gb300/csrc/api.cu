@@ -12,8 +12,7 @@
 namespace sp {
 template <class VT, class XT>
 int launch_spmv_typed(const SpmvArgs &a, bool vec, int max_blocks, cudaStream_t s);
-int launch_spmv_vty(const SpmvArgs &a, const double *V, int64_t ldv, int m, double *C, int64_t ldc, int max_blocks,
-                    cudaStream_t s);
+int launch_spmv_vty(const SpmvArgs &a, int max_blocks, cudaStream_t s);
 int spmv_scattered(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_opts &o, void *stream);
 }
 
@@ -695,13 +694,19 @@ int sp_spmv_vty(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_o
     a.eta = o.eta;
     a.partials = (double *)A->scratch->ptr;
     a.ticket = (unsigned *)((char *)A->scratch->ptr + A->scratch_bytes - 256);
+    a.wbounds_src = &P;
+    a.vty_V = (const double *)V->ptr;
+    a.vty_ldv = V->ld;
+    a.vty_m = m;
+    a.vty_C = C;
+    a.vty_ldc = ldc;
     for (int k = 0; k < kMaxTileW; ++k)
         a.gamma[k] = !shift || k >= w ? 0.0 : ((f & SP_SPMV_SHIFT) ? o.gamma[0] : o.gamma[k]);
     if (P.nrows == 0) {
         SP_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)ldc * m, (cudaStream_t)stream));
         return SP_OK;
     }
-    return launch_spmv_vty(a, (const double *)V->ptr, V->ld, m, C, ldc, max_blocks_of(A), (cudaStream_t)stream);
+    return launch_spmv_vty(a, max_blocks_of(A), (cudaStream_t)stream);
 }
 
 int sp_spmv_adjoint(sp_dense *dx, void *dvals, const sp_mat *A, const sp_dense *x, const sp_dense *g,

@@ -77,6 +77,13 @@ struct SpmvArgs {
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
     int32_t log2C;           // log2 of C when C is a power of two, else -1
     const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
+    // C = V^T y formed with the product (kernels with MV > 0): V is nrows x
+    // vty_m (row-major, leading dimension vty_ldv), C is vty_m x w (vty_ldc)
+    const double *vty_V;
+    int64_t vty_ldv;
+    int32_t vty_m;
+    double *vty_C;
+    int64_t vty_ldc;
     double gamma[kMaxTileW];
 };
 
@@ -619,6 +626,50 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
+// C = V^T y from the lanes' partial sums, in a fixed order like reduce_dots:
+// lanes of a column group by an xor tree, the warps of a block in order, the
+// blocks in order by the last block to arrive.  Value (p, k) is number
+// p w + k (at most 8 x 8 of the 3 x 32 slots per warp and per block).
+template <int CPL, int G, int MV>
+__device__ __forceinline__ void reduce_vty(const SpmvArgs &a, int k0, double (&v)[MV][CPL]) {
+    double (*sred)[3][kMaxTileW] = dot_smem();
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *mine = &sred[warp][0][0];
+#pragma unroll
+    for (int p = 0; p < MV; ++p)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) v[p][c] += __shfl_xor_sync(0xffffffffu, v[p][c], o);
+            if (lane < G && p < a.vty_m && k0 + c < a.w) mine[p * a.w + k0 + c] = v[p][c];
+        }
+    __syncthreads();
+    const int nv = a.vty_m * a.w;
+    const int nb = gridDim.x;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int wi = 0; wi < kMainWarps; ++wi) s += (&sred[wi][0][0])[t];
+        a.partials[(int64_t)t * nb + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(a.ticket, 1u) == (unsigned)nb - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int t = warp; t < nv; t += kMainWarps) {
+        const int p = t / a.w, k = t - p * a.w;
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += __ldcg(a.partials + (int64_t)t * nb + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) a.vty_C[(int64_t)p * a.vty_ldc + k] = s;
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
 // Swizzle of the block index before it picks its slice of the partition: with
 // SP_SWIZZLE blocks b, b + SMs, b + 2 SMs, ... (the blocks a one-wave launch
 // usually places on one SM) own consecutive slices, so each SM works on one
@@ -666,7 +717,7 @@ __device__ __forceinline__ void reduce_dots(const SpmvArgs &a, int k0, double (&
 // an unconditional operation and a select, and for float64 vectors that
 // operation occupies the float64 pipe (Laplacian 256^3: three of every eleven
 // float64 instructions per row were such).
-template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI>
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI, int MV = 0>
 __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? SP_MINB_W1 : WP < 8 ? 1 : sizeof(XT) == 8 ? SP_MINB_WIDE_F64 : SP_MINB_WIDE_F32))
     k_spmmv(const __grid_constant__ SpmvArgs a) {
     using AT = typename AccOf<VT, XT>::T;
@@ -708,6 +759,8 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
     const int nvalid = a.w - k0 < CPL ? a.w - k0 : CPL;
     const uint32_t f = a.flags;
     static_assert(EPI >= 2 || DM == 0, "compile-time epilogues 0 and 1 have no dots");
+    static_assert(MV == 0 || (DM == 0 && !MT && std::is_same<XT, double>::value),
+                  "V^T y: float64 vectors, no fused dots, one lane group per row");
     const bool shift = EPI == 3 || (EPI == 2 && (f & (SP_SPMV_SHIFT | SP_SPMV_VSHIFT)) != 0);
     const bool do_scale = EPI == 2 ? (f & SP_SPMV_SCALE) != 0 : EPI != 0;
     const bool do_axpby = EPI == 2 ? (f & SP_SPMV_AXPBY) != 0 : EPI != 0;
@@ -729,6 +782,13 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         if constexpr ((DM & 2) != 0) dxy[c] = DT(0);
         if constexpr ((DM & 4) != 0) dxx[c] = DT(0);
     }
+
+    // this lane's share of C = V^T y: V[i, p] y[i, k0 + c] summed over its rows
+    double vacc[MV > 0 ? MV : 1][MV > 0 ? CPL : 1];
+#pragma unroll
+    for (int p = 0; p < (MV > 0 ? MV : 1); ++p)
+#pragma unroll
+        for (int c = 0; c < (MV > 0 ? CPL : 1); ++c) vacc[p][c] = 0.0;
 
     const XT *__restrict__ xk = x + (int64_t)k0 * a.xcs;
 
@@ -883,6 +943,17 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             for (int c = 0; c < CPL; ++c) zo[c] = fma_rn(eta, t[c], mul_rn(delta, zo[c]));
             store_out<XT, CPL, VEC>(zp, a.zcs, nvalid, zo);
         }
+        if constexpr (MV > 0) {
+            const double *__restrict__ vr = a.vty_V + i * a.vty_ldv;
+#pragma unroll
+            for (int p = 0; p < MV; ++p) {
+                if (p < a.vty_m) {
+                    const double vv = __ldg(vr + p);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) vacc[p][c] = fma_rn(vv, (double)t[c], vacc[p][c]);
+                }
+            }
+        }
     };
 
     if (a.sched) {
@@ -968,6 +1039,7 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
         reduce_dots<CPL, G, DM, BANK>(a, k0, vyy, vxy, vxx);
     }
+    if constexpr (MV > 0) reduce_vty<CPL, G, MV>(a, k0, vacc);
 }
 
 // Host-side dispatch over the block width for one (value, vector) type pair.

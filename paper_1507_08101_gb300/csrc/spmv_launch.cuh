@@ -32,7 +32,7 @@ namespace sp {
 #define SP_CARVEOUT -1
 #endif
 
-template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI>
+template <class VT, class XT, int WP, bool VEC, int DM, bool MT, bool LS, int EPI, int MV = 0>
 static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s) {
     constexpr int CPL = cols_per_lane<XT, WP>();
     constexpr int G = WP / CPL;
@@ -40,9 +40,9 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     static int occ = 0;
     if (occ == 0) {
         if (SP_CARVEOUT >= 0)
-            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI, MV>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  SP_CARVEOUT);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI, MV>,
                                                                       kMainThreads, 0);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
@@ -76,7 +76,7 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.nsm = sms;
     b.log2_tpr = lt;
     b.log2C = ilog2_exact(a.C);
-    k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
+    k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI, MV><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -54,8 +54,8 @@ def test_vty_matches_oracle(cuda_ok, band, C, sigma, w, m):
     y2, z2 = torch.from_numpy(Y0.copy()).cuda(), torch.from_numpy(Z0.copy()).cuda()
     sellcs.spmv(mat, x, y2, alpha=0.5, gamma=gam, beta=-1.5, z=z2, delta=0.9, eta=0.1)
     torch.cuda.synchronize()
-    if C >= 32:  # one lane per row in both kernels
-        assert torch.equal(y2, y) and torch.equal(z2, z)
+    # the fused form is a variant of the same kernel: same row loops, same epilogue
+    assert torch.equal(y2, y) and torch.equal(z2, z)
     mat.close()
 
 
@@ -72,4 +72,30 @@ def test_vty_arguments(cuda_ok, band):
     with pytest.raises(sellcs.SpError) as e:
         sellcs.spmv_vty(mat, x, y, y, Cd[:2])  # V is y
     assert e.value.code == sellcs.SP_ERR_ARG
+    mat.close()
+
+
+@pytest.mark.parametrize("m", [1, 4, 8])
+def test_vty_full_size(cuda_ok, m):
+    """The irregular N = 2^21 workload at SELL-32-256 (the launch configuration
+    of the product benchmark) with V of m columns: y and z element by element,
+    C within its bound, all against the oracle."""
+    A, X, Y0, Z0 = gen.workload_irregular()
+    rng = np.random.default_rng(77 + m)
+    V = rng.uniform(-0.5, 0.5, (A.nrows, m))
+    mat = sellcs.SellMatrix(A, C=32, sigma=256)
+    x, y, z, v = (torch.from_numpy(a).cuda() for a in (X, Y0.copy(), Z0.copy(), V))
+    Cd = torch.full((m, 1), float("nan"), dtype=torch.float64, device="cuda")
+    kw = dict(alpha=0.5, gamma=0.1, beta=1.0)
+    sellcs.spmv_vty(mat, x, y, v, Cd, **kw, z=z, delta=0.9, eta=0.1)
+    torch.cuda.synchronize()
+    yr, _, zr = oracle.spmmv(A, X, **kw, y0=Y0, delta=0.9, eta=0.1, z0=Z0)
+    sc = oracle.spmmv_scale(A, X, **kw, y0=Y0)
+    tol = tol_for("f64", "f64", 0)
+    assert_close(y.cpu().numpy(), yr, sc, tol, "vty y")
+    assert_close(z.cpu().numpy(), zr, 0.9 * np.abs(Z0) + 0.1 * (np.abs(yr) + sc), tol, "vty z")
+    y2, e = np.reshape(yr, (A.nrows, 1)), np.reshape(tol * sc, (A.nrows, 1))
+    Cr = oracle.tsmttsm(V, y2)
+    bound = np.abs(V).T @ e + (gamma(A.nrows + 2100, U53) + 1e-15) * (np.abs(V).T @ (np.abs(y2) + e))
+    assert_close(Cd.cpu().numpy(), Cr, bound, 1.0, "vty C")
     mat.close()
