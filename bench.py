@@ -526,16 +526,21 @@ def secondary_anderson(peak, pairs=None):
     return out
 
 
-def secondary_powerlaw(peak):
+def secondary_powerlaw(peak, fixed=None):
     """Power-law N = 2^20, f32, width 4: forward product and backward
-    (A^T g through the transposed matrix + sampled dvals)."""
+    (A^T g through the transposed matrix + sampled dvals).  ``fixed`` =
+    (C, sigma, order) skips the autotuner (a profiler run, whose timings would
+    mislead the tuner)."""
     import torch
     from paper_1507_08101_gb300 import sellcs
     from workloads import generators as gen
     from paper_1507_08101_gb300 import autotune
     A, X, G = gen.workload_powerlaw()
     t0 = time.perf_counter()
-    tuned = autotune.tune_spmv(A, 4, "f32", "f32", with_transpose=True, cache_path=None)
+    if fixed:
+        tuned = {"C": int(fixed[0]), "sigma": int(fixed[1]), "order": fixed[2]}
+    else:
+        tuned = autotune.tune_spmv(A, 4, "f32", "f32", with_transpose=True, cache_path=None)
     tune_s = time.perf_counter() - t0
     m = sellcs.SellMatrix(A, C=tuned["C"], sigma=tuned["sigma"], dtype="f32", with_transpose=True,
                           order=tuned["order"])
@@ -1014,6 +1019,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--powerlaw-config", default=None,
+                    help="with --only powerlaw_adjoint: C:sigma:order instead of the autotuner's choice")
     ap.add_argument("--no-fp64-probe", action="store_true",
                     help="skip the float64 rate probe that runs after the timed region")
     ap.add_argument("--only", choices=["laplace", "laplace256", "anderson_w16", "powerlaw_adjoint", "cg_batch", "kpm",
@@ -1041,7 +1048,9 @@ def main():
                "anderson_w16": lambda p: secondary_anderson(
                    p, [tuple(q.split(":")) for q in args.pairs.split(",")] if args.pairs else None),
                "tsm": lambda p: secondary_tsm(p, tuple(args.pairs.split(",")) if args.pairs else ("f64", "f32")),
-               "powerlaw_adjoint": secondary_powerlaw, "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
+               "powerlaw_adjoint": lambda p: secondary_powerlaw(
+                   p, args.powerlaw_config.split(":") if args.powerlaw_config else None),
+               "cg_batch": secondary_cg_batch, "kpm": secondary_kpm,
                "permuted": secondary_permuted, "dist": secondary_dist,
                "layout": secondary_layout, "vty": secondary_vty}
         print(json.dumps({args.only: fns[args.only](load_peaks()[0])}), flush=True)

@@ -95,6 +95,11 @@ struct BatchArgs {
 #ifndef SP_BATCH_PREFETCH
 #define SP_BATCH_PREFETCH 0
 #endif
+// matrix loads: 1 always evict-first, 0 never, 2 only where a warp step reads
+// whole sectors (knob)
+#ifndef SP_BATCH_STREAM
+#define SP_BATCH_STREAM 2
+#endif
 // unroll depth of the row loop for 4-column lanes (knob)
 #ifndef SP_BATCH_UNROLL_WIDE
 #define SP_BATCH_UNROLL_WIDE SP_UNROLL_WIDE
@@ -111,6 +116,10 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
     constexpr int R = 32 / G;
     constexpr int U = CPL >= 4 ? SP_BATCH_UNROLL_WIDE : SP_UNROLL_NARROW / CPL;
     constexpr bool dots = (DM & 7) != 0;
+    // evict-first matrix loads only where one warp step reads whole 32-byte
+    // sectors of values and indices (R rows of a chunk column per step)
+    constexpr bool stream = SP_BATCH_STREAM == 1 || (SP_BATCH_STREAM == 2 && R * sizeof(int32_t) >= 32 &&
+                                                     R * sizeof(VT) >= 32);
     const int lt = u.log2_tpr;
     const int T = 1 << lt;
     const int gl = lane % G;
@@ -165,14 +174,14 @@ __device__ __forceinline__ void batch_unit(const BatchArgs &a, const BMat *__res
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
             int bad = 0;
-            row_product<VT, XT, AT, CPL, true, U>(val + cur.off, colp + cur.off, (int)C << lt, len_t, xk, w, 1,
-                                                  nvalid, acc, bad);
+            row_product<VT, XT, AT, CPL, true, U, false, stream>(val + cur.off, colp + cur.off, (int)C << lt, len_t,
+                                                                 xk, w, 1, nvalid, acc, bad);
             if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value) {
                 if (bad) {  // x outside the fast conversion's range: again with the conversion instruction
 #pragma unroll
                     for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-                    row_product<VT, XT, AT, CPL, true, U, true>(val + cur.off, colp + cur.off, (int)C << lt, len_t,
-                                                                xk, w, 1, nvalid, acc, bad);
+                    row_product<VT, XT, AT, CPL, true, U, true, stream>(val + cur.off, colp + cur.off, (int)C << lt,
+                                                                        len_t, xk, w, 1, nvalid, acc, bad);
                 }
             }
             bool epi = true;

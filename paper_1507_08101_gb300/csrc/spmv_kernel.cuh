@@ -251,6 +251,14 @@ __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
 template <class T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 #endif
+// The matrix stream: evict-first (ST) where every sector a step touches is
+// read whole by that step, else a normal load so that a sector read in parts
+// by consecutive steps stays cached between them.
+template <bool ST, class T>
+__device__ __forceinline__ T ld_mat(const T *p) {
+    if constexpr (ST) return ld_stream(p);
+    else return __ldg(p);
+}
 
 // Epilogue arithmetic written as explicit fused multiply-adds and rounded
 // products (never left to the compiler's contraction), so that each kernel
@@ -361,7 +369,7 @@ __device__ __forceinline__ void store_out(XT *p, int64_t cs, int nvalid, const X
 // `steps` multiply-adds, in entry order: a multiply-add under a false
 // predicate would cost as much as a real one on GB300's float64 pipe (a
 // predicated-off lane still occupies its slot of the warp instruction).
-template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT, bool ST = true>
 __device__ __forceinline__ void tail_steps(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                            int rest, int steps, const XT *__restrict__ xk, int64_t xrs,
                                            int64_t xcs, int nvalid, AT (&acc)[CPL], int &bad) {
@@ -373,8 +381,8 @@ __device__ __forceinline__ void tail_steps(const VT *__restrict__ vp, const int3
     for (int k = 0; k < U; ++k) {
         const int e = k - sh;
         const bool ok = e >= 0 && e < rest;
-        cc[k] = ok ? ld_stream(cp + (int64_t)e * C) : 0;
-        vv[k] = ok ? ld_stream(vp + (int64_t)e * C) : VT(0);
+        cc[k] = ok ? ld_mat<ST>(cp + (int64_t)e * C) : 0;
+        vv[k] = ok ? ld_mat<ST>(vp + (int64_t)e * C) : VT(0);
     }
     if (nvalid <= 0) return;
     XT xv[U][CPL];
@@ -431,7 +439,7 @@ static_assert(SP_DOT_RUN_F32 >= 1, "dot run length");
 #ifndef SP_LS_SPREAD_DOTS
 #define SP_LS_SPREAD_DOTS 0.15
 #endif
-template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false, bool ST = true>
 __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                                int len, int clen, const XT *__restrict__ xk, int64_t xrs,
                                                int64_t xcs, int nvalid, AT (&acc)[CPL], int &bad) {
@@ -442,8 +450,8 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool ok = j + u < len;
-            cc[u] = ok ? ld_stream(cp + (int64_t)u * C) : 0;
-            vv[u] = ok ? ld_stream(vp + (int64_t)u * C) : VT(0);
+            cc[u] = ok ? ld_mat<ST>(cp + (int64_t)u * C) : 0;
+            vv[u] = ok ? ld_mat<ST>(vp + (int64_t)u * C) : VT(0);
         }
         vp += (int64_t)U * C;
         cp += (int64_t)U * C;
@@ -460,7 +468,8 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
             }
         }
     }
-    if (clen > j) tail_steps<VT, XT, AT, CPL, VEC, U, EXACT>(vp, cp, C, len - j, clen - j, xk, xrs, xcs, nvalid, acc, bad);
+    if (clen > j)
+        tail_steps<VT, XT, AT, CPL, VEC, U, EXACT, ST>(vp, cp, C, len - j, clen - j, xk, xrs, xcs, nvalid, acc, bad);
 }
 
 // Row sums t[c] = sum_j val(s,j) * x[col(s,j), k0 + c] for the row in one slot.
@@ -468,7 +477,7 @@ __device__ __forceinline__ void row_product_ls(const VT *__restrict__ vp, const 
 // (len mod U) entries are issued the same way under a predicate, so a short
 // row (fewer than U entries) costs one round trip, not one per entry.  The
 // products are added in the order j = 0, 1, ..., len - 1 in every case.
-template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false, bool ST = true>
 __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                             int len, const XT *__restrict__ xk, int64_t xrs, int64_t xcs,
                                             int nvalid, AT (&acc)[CPL], int &bad) {
@@ -478,8 +487,8 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
         VT vv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            cc[u] = ld_stream(cp + (int64_t)u * C);
-            vv[u] = ld_stream(vp + (int64_t)u * C);
+            cc[u] = ld_mat<ST>(cp + (int64_t)u * C);
+            vv[u] = ld_mat<ST>(vp + (int64_t)u * C);
         }
         vp += (int64_t)U * C;
         cp += (int64_t)U * C;
@@ -497,7 +506,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
     // lanes run rows of their own lengths here, so no count shorter than U
     // bounds every lane's tail: all U steps, each under its lane's predicate
     const int rest = len - j;
-    if (rest > 0) tail_steps<VT, XT, AT, CPL, VEC, U, EXACT>(vp, cp, C, rest, U, xk, xrs, xcs, nvalid, acc, bad);
+    if (rest > 0) tail_steps<VT, XT, AT, CPL, VEC, U, EXACT, ST>(vp, cp, C, rest, U, xk, xrs, xcs, nvalid, acc, bad);
 }
 
 // row_product with the index and value loads one batch ahead: batch b + 1's
@@ -506,7 +515,7 @@ __device__ __forceinline__ void row_product(const VT *__restrict__ vp, const int
 // multiply-add is under its lane's predicate (j + u < len), which on the
 // float32 pipe costs little; the products are added in the order
 // j = 0, 1, ..., len - 1, so the sums equal row_product's bit for bit.
-template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false>
+template <class VT, class XT, class AT, int CPL, bool VEC, int U, bool EXACT = false, bool ST = true>
 __device__ __forceinline__ void row_product_pipe(const VT *__restrict__ vp, const int32_t *__restrict__ cp, int C,
                                                  int len, const XT *__restrict__ xk, int64_t xrs, int64_t xcs,
                                                  int nvalid, AT (&acc)[CPL], int &bad) {
@@ -515,8 +524,8 @@ __device__ __forceinline__ void row_product_pipe(const VT *__restrict__ vp, cons
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const bool ok = u < len;
-        cc[u] = ok ? ld_stream(cp + (int64_t)u * C) : 0;
-        vv[u] = ok ? ld_stream(vp + (int64_t)u * C) : VT(0);
+        cc[u] = ok ? ld_mat<ST>(cp + (int64_t)u * C) : 0;
+        vv[u] = ok ? ld_mat<ST>(vp + (int64_t)u * C) : VT(0);
     }
     for (int j = 0; j < len; j += U) {
         int32_t cn[U];
@@ -524,8 +533,8 @@ __device__ __forceinline__ void row_product_pipe(const VT *__restrict__ vp, cons
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool ok = j + U + u < len;
-            cn[u] = ok ? ld_stream(cp + (int64_t)(j + U + u) * C) : 0;
-            vn[u] = ok ? ld_stream(vp + (int64_t)(j + U + u) * C) : VT(0);
+            cn[u] = ok ? ld_mat<ST>(cp + (int64_t)(j + U + u) * C) : 0;
+            vn[u] = ok ? ld_mat<ST>(vp + (int64_t)(j + U + u) * C) : VT(0);
         }
         if (nvalid > 0) {
             XT xv[U][CPL];
@@ -741,6 +750,9 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
                                                                : SP_PREFETCH_META_F64 != 0)
                                                    : SP_PREFETCH_META_F32 != 0;
 
+    // evict-first matrix loads only where one warp step reads whole 32-byte
+    // sectors of values and indices (the step covers R rows of a chunk column)
+    constexpr bool ST = R * sizeof(int32_t) >= 32 && R * sizeof(VT) >= 32;
     // float accumulation: the row loop with its index and value loads one batch
     // ahead (measured faster for every pair but bfloat16 values with float32
     // vectors, which keeps the plain loop)
@@ -865,23 +877,25 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
             for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
             int bad = 0;
             if constexpr (LS)
-                row_product_ls<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                                        a.C << lt, len_t, (m.clen + T - 1) >> lt, xk, a.xrs, a.xcs,
-                                                        nvalid, acc, bad);
+                row_product_ls<VT, XT, AT, CPL, VEC, U, false, ST>(val + off + (int64_t)tt * a.C,
+                                                                   a.col + off + (int64_t)tt * a.C, a.C << lt, len_t,
+                                                                   (m.clen + T - 1) >> lt, xk, a.xrs, a.xcs, nvalid,
+                                                                   acc, bad);
             else if constexpr (pipe)
-                row_product_pipe<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C,
-                                                          a.col + off + (int64_t)tt * a.C, a.C << lt, len_t, xk,
-                                                          a.xrs, a.xcs, nvalid, acc, bad);
+                row_product_pipe<VT, XT, AT, CPL, VEC, U, false, ST>(val + off + (int64_t)tt * a.C,
+                                                                     a.col + off + (int64_t)tt * a.C, a.C << lt,
+                                                                     len_t, xk, a.xrs, a.xcs, nvalid, acc, bad);
             else
-                row_product<VT, XT, AT, CPL, VEC, U>(val + off + (int64_t)tt * a.C, a.col + off + (int64_t)tt * a.C,
-                                                     a.C << lt, len_t, xk, a.xrs, a.xcs, nvalid, acc, bad);
+                row_product<VT, XT, AT, CPL, VEC, U, false, ST>(val + off + (int64_t)tt * a.C,
+                                                                a.col + off + (int64_t)tt * a.C, a.C << lt, len_t, xk,
+                                                                a.xrs, a.xcs, nvalid, acc, bad);
             if constexpr (std::is_same<AT, float>::value && std::is_same<XT, double>::value) {
                 // an x element outside the fast conversion's range: this lane's
                 // share of the row again, with the conversion instruction
                 if (bad) {
 #pragma unroll
                     for (int c = 0; c < CPL; ++c) acc[c] = AT(0);
-                    row_product<VT, XT, AT, CPL, VEC, U, true>(val + off + (int64_t)tt * a.C,
+                    row_product<VT, XT, AT, CPL, VEC, U, true, ST>(val + off + (int64_t)tt * a.C,
                                                                a.col + off + (int64_t)tt * a.C, a.C << lt, len_t, xk,
                                                                a.xrs, a.xcs, nvalid, acc, bad);
                 }
