@@ -32,9 +32,10 @@
  *    2^31 - 1 nonzeros per row (local indices are 32-bit, Sec. "Sparse matrix
  *    storage", local vs global indices); stored entries are counted in int64.
  *  - Thread safety: distinct handles may be used from distinct host threads.
- *    Calls that use the same matrix handle with dot products requested must be
- *    ordered (same stream, or synchronised): they share the handle's
- *    reduction scratch.
+ *    Calls that use the same matrix handle must be ordered (same stream, or
+ *    synchronised): they share the handle's scratch (the partial sums of the
+ *    fused reductions and the counters of the dynamic row order that
+ *    products on blocks of width 16 or more use).
  */
 #ifndef SELLCS_H
 #define SELLCS_H

@@ -96,8 +96,9 @@ extern "C" int sp_spmv_noalloc(const void *val, sp_dtype val_dtype, const int32_
     NoAllocAddr na;
     SP_TRY(noalloc_setup(&na));
     cudaStream_t s = (cudaStream_t)stream;
-    // the ticket must start at zero; a call that did not finish could have left it set
-    SP_CUDA(cudaMemsetAsync(na.ticket, 0, sizeof(unsigned), s));
+    // the ticket and the dynamic-order counters (words 0..2) must start at
+    // zero; a call that did not finish could have left them set
+    SP_CUDA(cudaMemsetAsync(na.ticket, 0, 3 * sizeof(unsigned), s));
 
     const int64_t nchunks = (nrows + C - 1) / C;
     SpmvArgs a{};

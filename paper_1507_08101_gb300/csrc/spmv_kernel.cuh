@@ -76,6 +76,7 @@ struct SpmvArgs {
     int32_t nsm;             // SMs the grid was sized for
     int32_t log2_tpr;        // threads per row T = 2^log2_tpr (lanes splitting one row's entries)
     int32_t log2C;           // log2 of C when C is a power of two, else -1
+    int32_t dyn_grab;        // > 0: warps take runs of this many slots from a counter (no dots)
     const Pattern *wbounds_src;  // host side only: where the launcher finds the partition
     // C = V^T y formed with the product (kernels with MV > 0): V is nrows x
     // vty_m (row-major, leading dimension vty_ldv), C is vty_m x w (vty_ldc)
@@ -970,6 +971,31 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
     };
 
+    if constexpr (DM == 0 && MV == 0) {
+        if (a.dyn_grab > 0) {
+            // dynamic order (products without fused reductions, whose results do
+            // not depend on which warp computes which rows): each warp takes the
+            // next run of dyn_grab slots from a counter until none is left; the
+            // last warp to finish resets the counter for the next launch
+            unsigned *next = a.ticket + 1, *done = a.ticket + 2;
+            const int64_t nruns = (a.nslots + a.dyn_grab - 1) / a.dyn_grab;
+            for (;;) {
+                unsigned r = 0;
+                if (lane == 0) r = atomicAdd(next, 1u);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if ((int64_t)r >= nruns) break;
+                const int64_t s0 = (int64_t)r * a.dyn_grab;
+                const int64_t s1 = s0 + a.dyn_grab < a.nslots ? s0 + a.dyn_grab : a.nslots;
+                for (int64_t s = s0 + rw; s < s1; s += Rr) slot(meta_of(s));
+            }
+            __threadfence();
+            if (lane == 0 && atomicAdd(done, 1u) == gridDim.x * (unsigned)kMainWarps - 1u) {
+                *next = 0u;
+                *done = 0u;
+            }
+            return;
+        }
+    }
     if (a.sched) {
         // moving front: in round r this warp takes one 32-slot block of the
         // run of adjacent blocks the whole grid covers in that round

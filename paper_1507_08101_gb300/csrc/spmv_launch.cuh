@@ -26,6 +26,18 @@ namespace sp {
 #define SP_FRONT_X_L2_FRAC 0.5
 #endif
 
+// Dynamic row order for products without fused reductions (knob) and the
+// number of slot runs per warp it aims at.
+#ifndef SP_DYN
+#define SP_DYN 1
+#endif
+#ifndef SP_DYN_RUNS_PER_WARP
+#define SP_DYN_RUNS_PER_WARP 16
+#endif
+#ifndef SP_DYN_MIN_WP
+#define SP_DYN_MIN_WP 16
+#endif
+
 // Preferred shared-memory carveout (percent of the unified L1/shared array
 // given to shared memory); negative: leave the driver's choice.
 #ifndef SP_CARVEOUT
@@ -76,6 +88,21 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.nsm = sms;
     b.log2_tpr = lt;
     b.log2C = ilog2_exact(a.C);
+    // products without fused reductions on wide row-major blocks take their
+    // rows in dynamic order: runs of whole 32-slot blocks, about
+    // SP_DYN_RUNS_PER_WARP runs per warp.  Measured faster for w = 16
+    // (Anderson: float32 179 -> 140 us, float64 540 -> 515 us) and slower
+    // where x is reused from L1 by the adjacent ranges of one SM's warps
+    // (float32 w = 4: 46 -> 71 us; power-law forward 63 -> 78 us).
+    b.dyn_grab = 0;
+    if constexpr (DM == 0 && MV == 0 && VEC && WP >= SP_DYN_MIN_WP) {
+        if (SP_DYN != 0 && a.ticket) {
+            const int64_t warps = grid * kMainWarps;
+            int64_t g = (a.nslots + warps * SP_DYN_RUNS_PER_WARP - 1) / (warps * SP_DYN_RUNS_PER_WARP);
+            g = (g + 31) / 32 * 32;
+            b.dyn_grab = (int32_t)(g < 32 ? 32 : g);
+        }
+    }
     k_spmmv<VT, XT, WP, VEC, DM, MT, LS, EPI, MV><<<(unsigned)grid, kMainThreads, 0, s>>>(b);
     SP_CUDA(cudaGetLastError());
     return SP_OK;

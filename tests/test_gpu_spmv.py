@@ -215,6 +215,23 @@ def test_work_order_does_not_change_results(cuda_ok, irregular_large, vdt, xdt, 
     assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
 
 
+@pytest.mark.parametrize("vdt,xdt", [("f64", "f64"), ("f32", "f32"), ("bf16", "f64")])
+@pytest.mark.parametrize("w", [16, 32])
+def test_dynamic_order_repeats_and_matches_static(cuda_ok, irregular_large, vdt, xdt, w):
+    """Products on wide row-major blocks without fused reductions take their
+    rows in dynamic order (warps draw runs of slots from a counter that the
+    last warp resets).  Three calls in a row give the same bits, the same bits
+    as the product with dot products (static order), and match the oracle."""
+    A = irregular_large
+    m = sellcs.SellMatrix(A, C=32, sigma=256, dtype=vdt)
+    plain = {"scale", "shift", "axpby", "chain"}
+    ys = [run_case(A, 32, 256, w, plain, vdt=vdt, xdt=xdt, mat=m, seed=11)[0] for _ in range(3)]
+    y_static = run_case(A, 32, 256, w, plain | {"dot_yy"}, vdt=vdt, xdt=xdt, mat=m, seed=11)[0]
+    m.close()
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+    assert np.array_equal(ys[0], y_static)
+
+
 def test_float64_extreme_magnitudes(cuda_ok):
     """x entries and matrix values of extreme magnitude (1e60, 3e-30, 1e45
     scaling), exact zeros and an infinity: the float64 tolerance holds and a
