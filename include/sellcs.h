@@ -35,7 +35,7 @@
  *    Calls that use the same matrix handle must be ordered (same stream, or
  *    synchronised): they share the handle's scratch (the partial sums of the
  *    fused reductions and the counters of the dynamic row order that
- *    products on blocks of width 16 or more use).
+ *    products on row-major blocks of more than 4 columns use).
  */
 #ifndef SELLCS_H
 #define SELLCS_H

@@ -35,7 +35,7 @@ namespace sp {
 #define SP_DYN_RUNS_PER_WARP 16
 #endif
 #ifndef SP_DYN_MIN_WP
-#define SP_DYN_MIN_WP 16
+#define SP_DYN_MIN_WP 8
 #endif
 
 // Preferred shared-memory carveout (percent of the unified L1/shared array
@@ -90,10 +90,11 @@ static int launch_spmv_variant(const SpmvArgs &a, int max_blocks, cudaStream_t s
     b.log2C = ilog2_exact(a.C);
     // products without fused reductions on wide row-major blocks take their
     // rows in dynamic order: runs of whole 32-slot blocks, about
-    // SP_DYN_RUNS_PER_WARP runs per warp.  Measured faster for w = 16
-    // (Anderson: float32 179 -> 140 us, float64 540 -> 515 us) and slower
-    // where x is reused from L1 by the adjacent ranges of one SM's warps
-    // (float32 w = 4: 46 -> 71 us; power-law forward 63 -> 78 us).
+    // SP_DYN_RUNS_PER_WARP runs per warp.  Measured faster for w = 8 and 16
+    // (Anderson: float32 105 -> 85 and 179 -> 140 us, float64 274 -> 264 and
+    // 540 -> 515 us) and slower where x is reused from L1 by the adjacent
+    // ranges of one SM's warps (float32 w = 4: 46 -> 71 us; power-law forward
+    // 63 -> 78 us).
     b.dyn_grab = 0;
     if constexpr (DM == 0 && MV == 0 && VEC && WP >= SP_DYN_MIN_WP) {
         if (SP_DYN != 0 && a.ticket) {

@@ -216,7 +216,7 @@ def test_work_order_does_not_change_results(cuda_ok, irregular_large, vdt, xdt, 
 
 
 @pytest.mark.parametrize("vdt,xdt", [("f64", "f64"), ("f32", "f32"), ("bf16", "f64")])
-@pytest.mark.parametrize("w", [16, 32])
+@pytest.mark.parametrize("w", [8, 16, 32])
 def test_dynamic_order_repeats_and_matches_static(cuda_ok, irregular_large, vdt, xdt, w):
     """Products on wide row-major blocks without fused reductions take their
     rows in dynamic order (warps draw runs of slots from a counter that the
