@@ -1,5 +1,6 @@
 // C ABI (include/sellcs.h): argument checking, memory ownership and dispatch.
 // All arithmetic of the product runs in the kernels of the other units.
+#include <atomic>
 #include <stdio.h>
 
 #include <algorithm>
@@ -37,6 +38,23 @@ int device_sm_count(int *n) {
     if (!cached[dev]) SP_CUDA(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
     *n = cached[dev];
     return SP_OK;
+}
+
+void pool_keep_memory() {
+    static std::atomic<bool> done[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    if (done[dev].load(std::memory_order_acquire)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev].store(true, std::memory_order_release);
 }
 
 size_t device_l2_bytes() {
@@ -698,6 +716,7 @@ int sp_spmv_vty(sp_dense *y, const sp_mat *A, const sp_dense *x, const sp_spmv_o
     a.vty_V = (const double *)V->ptr;
     a.vty_ldv = V->ld;
     a.vty_m = m;
+    a.vty_vec2 = ((uintptr_t)V->ptr % 16 == 0 && V->ld % 2 == 0) ? 1 : 0;
     a.vty_C = C;
     a.vty_ldc = ldc;
     for (int k = 0; k < kMaxTileW; ++k)

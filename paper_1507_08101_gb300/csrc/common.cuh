@@ -44,12 +44,22 @@ using DevBufPtr = std::shared_ptr<DevBuf>;
 int dev_alloc(DevBufPtr &out, size_t bytes, cudaStream_t s);
 
 // Temporary device buffer (stream-ordered allocation, freed on the stream).
+// The device's default memory pool keeps what stream-ordered temporaries
+// free (release threshold: unlimited) instead of returning it at every
+// synchronisation, so the next call's temporaries need no new mapping.
+// Set once per device (knob SP_POOL_KEEP).
+#ifndef SP_POOL_KEEP
+#define SP_POOL_KEEP 1
+#endif
+void pool_keep_memory();
+
 struct Tmp {
     void *p = nullptr;
     cudaStream_t s;
     explicit Tmp(cudaStream_t st) : s(st) {}
     int alloc(size_t bytes) {
         if (!bytes) bytes = 16;
+        if (SP_POOL_KEEP) pool_keep_memory();
         cudaError_t e = cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();

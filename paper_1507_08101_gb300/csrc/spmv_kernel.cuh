@@ -83,6 +83,7 @@ struct SpmvArgs {
     const double *vty_V;
     int64_t vty_ldv;
     int32_t vty_m;
+    int32_t vty_vec2;  // rows of V start on 16 bytes: V read as pairs of doubles
     double *vty_C;
     int64_t vty_ldc;
     double gamma[kMaxTileW];
@@ -699,6 +700,10 @@ __device__ __forceinline__ void reduce_vty(const SpmvArgs &a, int k0, double (&v
 #ifndef SP_EARLY_EPI_F32
 #define SP_EARLY_EPI_F32 1
 #endif
+// V^T y: rows of V read as pairs of doubles where they are 16-byte aligned (knob)
+#ifndef SP_VTY_VEC2
+#define SP_VTY_VEC2 1
+#endif
 // float-accumulated products: row loop with loads one batch ahead (knob)
 #ifndef SP_PIPE_F32
 #define SP_PIPE_F32 1
@@ -960,13 +965,27 @@ __global__ void __launch_bounds__(kMainThreads, kMainWarps > 8 ? 1 : (WP == 1 ? 
         }
         if constexpr (MV > 0) {
             const double *__restrict__ vr = a.vty_V + i * a.vty_ldv;
+            auto add = [&](int p, double vv) {
 #pragma unroll
-            for (int p = 0; p < MV; ++p) {
-                if (p < a.vty_m) {
-                    const double vv = __ldg(vr + p);
+                for (int c = 0; c < CPL; ++c) vacc[p][c] = fma_rn(vv, (double)t[c], vacc[p][c]);
+            };
+            // pairs measured faster for m <= 4 (231 -> 228 us at m = 4) and
+            // slower at m = 8 (260 -> 263 us: more registers live)
+            if (MV >= 2 && MV <= 4 && SP_VTY_VEC2 != 0 && a.vty_vec2) {
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) vacc[p][c] = fma_rn(vv, (double)t[c], vacc[p][c]);
+                for (int p = 0; p + 1 < MV; p += 2) {
+                    if (p + 1 < a.vty_m) {
+                        const double2 v2 = __ldg(reinterpret_cast<const double2 *>(vr + p));
+                        add(p, v2.x);
+                        add(p + 1, v2.y);
+                    } else if (p < a.vty_m) {
+                        add(p, __ldg(vr + p));
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int p = 0; p < MV; ++p)
+                    if (p < a.vty_m) add(p, __ldg(vr + p));
             }
         }
     };
