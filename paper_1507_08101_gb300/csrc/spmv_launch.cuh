@@ -39,7 +39,7 @@ namespace sp {
 #endif
 
 // Preferred shared-memory carveout (percent of the unified L1/shared array
-// given to shared memory); negative: leave the driver's choice.
+// given to shared memory); negative: leave the CUDA default.
 #ifndef SP_CARVEOUT
 #define SP_CARVEOUT -1
 #endif
