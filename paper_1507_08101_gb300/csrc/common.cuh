@@ -204,6 +204,7 @@ size_t device_l2_bytes();
 int build_partition(Pattern &P, cudaStream_t s);
 constexpr int kPartWarps = 8;  // warps per block of the partitioned kernels
 constexpr int kSchedCtaWarps = 32;  // warps per CTA the front schedule is built for
+constexpr int kSchedResidentCtas = 1;  // resident CTAs per SM the front schedule is built for
 constexpr int kMaxOcc = 8;     // resident blocks per SM covered by the partition table
 // Partition table for a grid of `warps` resident warps, or null when that is
 // not kPartWarps * b * SMs for b <= kMaxOcc (then the kernels fall back to a

@@ -428,6 +428,21 @@ __global__ void k_partition(const int64_t *__restrict__ prefix, int64_t nb32, in
     }
 }
 
+// Stable insertion sort of a short array (the 32 blocks or warps of one CTA):
+// the same order as std::stable_sort, without its temporary buffer.
+template <class Less>
+static void stable_small_sort(int32_t *a, int n, Less less) {
+    for (int i = 1; i < n; ++i) {
+        const int32_t v = a[i];
+        int j = i;
+        while (j > 0 && less(v, a[j - 1])) {
+            a[j] = a[j - 1];
+            --j;
+        }
+        a[j] = v;
+    }
+}
+
 int build_partition(Pattern &P, cudaStream_t s) {
     int sms = 1;
     SP_TRY(device_sm_count(&sms));
@@ -469,8 +484,12 @@ int build_partition(Pattern &P, cudaStream_t s) {
     }
     P.bounds_sms = sms;
 
-    // moving-front schedules, for the grids a kSchedCtaWarps-warp kernel runs
-    // (one or two resident CTAs per SM)
+    // moving-front schedule, for the grid the product kernel runs: one
+    // resident kSchedCtaWarps-warp CTA per SM (every product kernel holds 56 to
+    // 64 registers per thread at 1024 threads, so a second CTA never fits; a
+    // grid without a table takes the contiguous ranges instead).  Building
+    // the table for two CTAs per SM as well cost about 3.5 ms of host time per
+    // matrix of 2M rows.
     if (nb32 > 0) {
         std::vector<int64_t> c(nb32);
         SP_CUDA(cudaMemcpyAsync(c.data(), cost.p, nb32 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -478,7 +497,7 @@ int build_partition(Pattern &P, cudaStream_t s) {
         std::vector<int32_t> table;
         for (int b = 1; b <= kMaxOcc; ++b) {
             const int64_t W = (int64_t)kPartWarps * b * sms;
-            if (W % kSchedCtaWarps || (b * kPartWarps) % kSchedCtaWarps) continue;  // whole CTAs per SM only
+            if (b * kPartWarps != kSchedCtaWarps * kSchedResidentCtas) continue;
             const int64_t rounds = (nb32 + W - 1) / W;
             P.sched_off[b] = (int64_t)table.size();
             P.sched_rounds[b] = (int32_t)rounds;
@@ -511,8 +530,8 @@ int build_partition(Pattern &P, cudaStream_t s) {
                     if (!n) continue;
                     int64_t *ld = load.data() + cta * kSchedCtaWarps;
                     for (int j = 0; j < kSchedCtaWarps; ++j) wrp[j] = j;
-                    std::stable_sort(blk, blk + n, [&](int32_t x, int32_t y) { return c[x] > c[y]; });
-                    std::stable_sort(wrp, wrp + kSchedCtaWarps, [&](int32_t x, int32_t y) { return ld[x] < ld[y]; });
+                    stable_small_sort(blk, n, [&](int32_t x, int32_t y) { return c[x] > c[y]; });
+                    stable_small_sort(wrp, kSchedCtaWarps, [&](int32_t x, int32_t y) { return ld[x] < ld[y]; });
                     for (int i = 0; i < n; ++i) {
                         t[r * W + cta * kSchedCtaWarps + wrp[i]] = blk[i];
                         ld[wrp[i]] += c[blk[i]];
